@@ -1,0 +1,299 @@
+"""Benchmark: eigensolves/s of the batched 3x3 symmetric eigensolver on GB300.
+
+Workload (one "step"): the 2^24-matrix mixed-difficulty FP64 batch (60 %
+iid N(0,1), 20 % clustered Q diag(1, 1+10^-k, -1) Q^T, 10 % near-diagonal,
+10 % exact diagonals with repeats, each scaled by 10^U(-50,50)), solved for
+eigenvalues and eigenvectors by one call of the C ABI.  Inputs (805 MB) and
+outputs (1.6 GB) are far larger than the 129 MB L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own
+2^24 batch (weak scaling, no collective on the data path); the time is the
+max over ranks.  ``--impl reference`` times the CPU FP64 oracle on the host
+cores instead (a bounded sample of the same workload).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "eigensolves/s at 2^24 batch (FP64 & FP32), % roofline; serving p50/p99 latency"
+UNIT = "eigensolves/s"
+N_MATRICES = 1 << 24
+BYTES_PER_MATRIX_F64 = 48 + 24 + 72  # packed input + eigenvalues + eigenvectors
+# Algorithmic FP64 operations per matrix of the mixed batch (add/sub + mul +
+# div + sqrt of the paper's method as the oracle's counting scalar executes
+# it, mean over the batch; tests/test_bench_constants.py re-derives it).
+FLOPS_PER_MATRIX_F64 = 289.0
+# FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz.
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["native", "reference"], default="native")
+    p.add_argument("--n", type=int, default=N_MATRICES, help=argparse.SUPPRESS)
+    p.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        with open(MEASURED_PEAKS) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(A: np.ndarray, sample: int, seconds_hint: float = 0.0) -> dict:
+    """The CPU FP64 oracle (as it stands) over all host cores on a bounded
+    sample of the workload."""
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    sub = np.ascontiguousarray(A[:sample])
+    _, _, secs = oracle.syev3_timed(sub, cores)
+    return {"value": sample / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} matrices of the 2^24 mixed FP64 batch, std::thread over {cores} cores, "
+                      f"{secs:.2f} s wall"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1806_06698_gb300 import inputs
+
+    A, _ = inputs.mixed(args.n)
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    sample = min(args.n, 1 << 21)
+    times = []
+    for i in range(args.warmup + args.steps):
+        lo = (i * sample) % max(1, args.n - sample + 1)
+        sub = np.ascontiguousarray(A[lo:lo + sample])
+        _, _, secs = oracle.syev3_timed(sub, cores)
+        if i >= args.warmup:
+            times.append(secs)
+    tot = sum(times)
+    value = sample * len(times) / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "mixed FP64 batch (2^24 recipe), CPU oracle on a bounded sample",
+                   "sample_per_step": sample, "threads": cores},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} matrices of the 2^24 mixed FP64 batch per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import torch
+
+    from paper_1806_06698_gb300 import build, inputs, syev3
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    build.build()
+    n = args.n
+    A_np, _ = inputs.mixed(n, seed=inputs.SEED_BASE + 1 + rank)
+    A = torch.from_numpy(A_np).to(dev)
+    lam = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    U = torch.empty((n, 3, 3), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    def step():
+        syev3.syev3_batched(A, out=(lam, U), stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        ev[2 * i].record(stream)
+        step()
+        ev[2 * i + 1].record(stream)
+    t1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    total_ms = t0.elapsed_time(t1)
+    kernel_ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps)]
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * n * args.steps / (total_ms * 1e-3)
+
+    # End to end through the public API with host buffers: pinned H2D of the
+    # step's inputs, the solve, D2H of eigenvalues and eigenvectors.
+    A_host = torch.from_numpy(A_np).pin_memory()
+    lam_host = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    U_host = torch.empty((n, 3, 3), dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+
+    def e2e_step():
+        A.copy_(A_host, non_blocking=True)
+        syev3.syev3_batched(A, out=(lam, U), stream=stream)
+        lam_host.copy_(lam, non_blocking=True)
+        U_host.copy_(U, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = ws * n * e2e_steps / (e2e_ms * 1e-3)
+
+    if rank == 0:
+        kms = statistics.mean(kernel_ms)
+        achieved = FLOPS_PER_MATRIX_F64 * n / (kms * 1e-3) / 1e9  # GFLOP/s
+        roofline = {"bound": "alu", "achieved": achieved / 1e3, "peak": FP64_PEAK_GFLOPS / 1e3,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                    "kernel": "k_syev3_f64", "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                    "hbm_frac_of_measured": (BYTES_PER_MATRIX_F64 * n / (kms * 1e-3) / 1e9) /
+                    load_peaks().get("hbm_gbs", 6686.1)}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "2^24 mixed-difficulty FP64 batch (60% N(0,1), 20% clustered, 10% "
+                                   "near-diagonal, 10% exact diagonal w/ repeats, x10^U(-50,50))",
+                       "n_per_gpu": n, "outputs": "eigenvalues + eigenvectors",
+                       "l2": "inputs and outputs > L2 (805 MB in, 1.6 GB out); no flush needed",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": roofline,
+            "gpu_launches": args.steps,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 48,
+                    "d2h_bytes_per_step": n * 96},
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(A_np, min(n, 1 << 22))
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

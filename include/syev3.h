@@ -1,0 +1,105 @@
+/* syev3.h -- C ABI of the GB300 batched 3x3 real symmetric eigensolver.
+ *
+ * The method is C. F. Borges, "Solving the 3x3 Real Symmetric Eigenproblem"
+ * (arXiv 1806.06698): an ordered Jacobi rotation in the (1,2)-plane reduces
+ * each matrix to an arrow (Sec. 1); the arrow is tested for beta-, combo- and
+ * numerical deflation and deflated arrows go to a 2x2 solve (Sec. 1.1);
+ * otherwise the Borges-Gragg zero finder (Sec. 1.4.1) gives the shifted
+ * extreme eigenvalues mu and nu, the middle one follows from the trace and
+ * the eigenvectors from closed forms (Sec. 1.2).
+ *
+ * Conventions shared by every entry point:
+ *  - A matrix is passed as its packed upper triangle, 6 values in the order
+ *    (a11, a22, a33, a12, a13, a23); n matrices are n consecutive records
+ *    (array of structures, no padding).
+ *  - Eigenvalues: 3 per matrix, ascending.
+ *  - Eigenvectors: a row-major 3x3 per matrix whose column k is the unit
+ *    eigenvector of eigenvalue k (the torch.linalg.eigh convention); each
+ *    column's largest-magnitude component is positive (first one on ties).
+ *  - Pointers named d_* / device buffers are CUDA device memory (or managed
+ *    memory) on the current device, allocated and owned by the caller; the
+ *    library never frees or keeps them.  Buffers must be 8-byte aligned
+ *    (FP64) or 4-byte aligned (FP32); 16-byte alignment selects the bulk-copy
+ *    (TMA) input path and vector stores.
+ *  - Calls are asynchronous on `stream` (NULL = the legacy default stream)
+ *    unless stated otherwise; errors detected on the host are returned
+ *    before anything is launched.
+ *  - A record with a NaN or Inf entry yields NaN eigenvalues and vectors.
+ *  - The zero finder is capped at 64 steps; a capped lane keeps its best
+ *    iterate (it never traps) and is counted when counters are supplied.
+ */
+#ifndef SYEV3_H
+#define SYEV3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ABI-identical to cudaStream_t. */
+typedef struct CUstream_st* syev3_stream_t;
+
+/* Element type of every floating-point buffer of a call. */
+typedef enum {
+  SYEV3_F64 = 0,             /* binary64 in and out */
+  SYEV3_F32 = 1,             /* binary32 in and out, plain FP32 arithmetic */
+  SYEV3_F32_COMPENSATED = 2  /* binary32 in and out; compensated FP32 with FP64 refinement of flagged lanes */
+} syev3_dtype;
+
+typedef enum {
+  SYEV3_OK = 0,
+  SYEV3_EINVAL = 1,  /* bad argument: nothing was launched */
+  SYEV3_ECUDA = 2,   /* a CUDA call failed (syev3_last_cuda_error() has the code) */
+  SYEV3_ENOCONV = 3, /* reserved: reported through counters, never returned by a launch */
+  SYEV3_ETIMEOUT = 4 /* a device-side wait ran out (see syev3_device_flags) */
+} syev3_status;
+
+/* Library ABI version (this header: 1). */
+int syev3_abi_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char* syev3_status_string(int status);
+
+/* The cudaError_t of the most recent SYEV3_ECUDA on this host thread. */
+int syev3_last_cuda_error(void);
+
+/* syev3_batched -- eigenvalues and eigenvectors of n packed symmetric 3x3
+ * matrices (Borges Secs. 1-1.4.1).
+ *   A_packed6 : device, n x 6 of `dtype`, read only.
+ *   n         : number of matrices, >= 0; n == 0 is a no-op returning SYEV3_OK.
+ *   lambda    : device, n x 3 of `dtype`, written (ascending eigenvalues).
+ *   U         : device, n x 9 of `dtype`, written (eigenvector columns), or
+ *               NULL to compute eigenvalues only.
+ *   dtype     : a syev3_dtype.
+ *   stream    : CUDA stream the work is ordered on.
+ * Returns SYEV3_EINVAL (NULL A or lambda, n < 0, bad dtype, misaligned or
+ * overlapping buffers) or SYEV3_ECUDA (launch failure); SYEV3_OK otherwise.
+ * The SYEV3_F32_COMPENSATED path needs scratch; this entry point takes it
+ * from the stream-ordered allocator (cudaMallocAsync) of the current device.
+ */
+int syev3_batched(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype,
+                  syev3_stream_t stream);
+
+/* syev3_batched_ex -- syev3_batched with optional counters.
+ *   d_counters : device, 4 x uint64, or NULL.  When given, the kernels add
+ *                [0] lanes whose zero finder hit the step cap,
+ *                [1] lanes with a non-finite input entry,
+ *                [2] lanes refined in FP64 (SYEV3_F32_COMPENSATED only),
+ *                [3] reserved (0).
+ *                The caller zeroes them; they accumulate across calls.
+ */
+int syev3_batched_ex(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype,
+                     uint64_t* d_counters, syev3_stream_t stream);
+
+/* Device-side status bits of the current device, OR-ed over all launches
+ * since the last call, then cleared (synchronises the device).
+ *   bit 0: a bulk-copy wait timed out (SYEV3_ETIMEOUT). */
+int syev3_device_flags(uint32_t* flags);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SYEV3_H */

@@ -1,0 +1,112 @@
+// syev3_api.cu -- the extern "C" boundary of libsyev3 (declared in
+// include/syev3.h): argument checks on the host, then one launch on the
+// caller's stream.  Nothing here computes; every step runs in the kernels.
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/syev3.h"
+#include "internal.h"
+
+namespace {
+
+thread_local int t_last_cuda_error = 0;
+
+int cuda_fail(cudaError_t e) {
+  t_last_cuda_error = (int)e;
+  return SYEV3_ECUDA;
+}
+
+size_t elem_size(int dtype) { return dtype == SYEV3_F64 ? 8 : 4; }
+
+bool valid_dtype(int dtype) {
+  return dtype == SYEV3_F64 || dtype == SYEV3_F32 || dtype == SYEV3_F32_COMPENSATED;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  if (a == nullptr || b == nullptr) return false;
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + nb && y < x + na;
+}
+
+// Device-accessible memory only: device, managed, or host memory registered
+// with (or allocated by) CUDA.  Plain pageable host memory is refused.
+bool device_accessible(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged ||
+         (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr);
+}
+
+int check_forward(const void* A, int64_t n, const void* lam, const void* U, int dtype) {
+  if (!valid_dtype(dtype) || n < 0) return SYEV3_EINVAL;
+  if (n == 0) return SYEV3_OK;
+  if (A == nullptr || lam == nullptr) return SYEV3_EINVAL;
+  const size_t es = elem_size(dtype);
+  if (!aligned(A, es) || !aligned(lam, es) || (U && !aligned(U, es))) return SYEV3_EINVAL;
+  const size_t nb_A = (size_t)n * 6 * es, nb_l = (size_t)n * 3 * es, nb_U = (size_t)n * 9 * es;
+  if (overlap(A, nb_A, lam, nb_l) || overlap(A, nb_A, U, nb_U) || overlap(lam, nb_l, U, nb_U))
+    return SYEV3_EINVAL;
+  if (!device_accessible(A) || !device_accessible(lam) || (U && !device_accessible(U))) return SYEV3_EINVAL;
+  return SYEV3_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int syev3_abi_version(void) { return 1; }
+
+const char* syev3_status_string(int status) {
+  switch (status) {
+    case SYEV3_OK: return "SYEV3_OK";
+    case SYEV3_EINVAL: return "SYEV3_EINVAL: invalid argument";
+    case SYEV3_ECUDA: return "SYEV3_ECUDA: CUDA call failed";
+    case SYEV3_ENOCONV: return "SYEV3_ENOCONV: zero finder hit its step cap";
+    case SYEV3_ETIMEOUT: return "SYEV3_ETIMEOUT: a device-side wait ran out";
+    default: return "SYEV3: unknown status";
+  }
+}
+
+int syev3_last_cuda_error(void) { return t_last_cuda_error; }
+
+int syev3_batched_ex(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype, uint64_t* d_counters,
+                     syev3_stream_t stream) {
+  const int st = check_forward(A_packed6, n, lambda, U, dtype);
+  if (st != SYEV3_OK || n == 0) return st;
+  if (d_counters && (!aligned(d_counters, 8) || !device_accessible(d_counters))) return SYEV3_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  auto* ctr = reinterpret_cast<unsigned long long*>(d_counters);
+  cudaError_t e;
+  switch (dtype) {
+    case SYEV3_F64:
+      e = syev3::launch_f64(static_cast<const double*>(A_packed6), n, static_cast<double*>(lambda),
+                            static_cast<double*>(U), ctr, s);
+      break;
+    default:
+      return SYEV3_EINVAL;  // FP32 paths are added by their own translation units
+  }
+  return e == cudaSuccess ? SYEV3_OK : cuda_fail(e);
+}
+
+int syev3_batched(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype, syev3_stream_t stream) {
+  return syev3_batched_ex(A_packed6, n, lambda, U, dtype, nullptr, stream);
+}
+
+int syev3_device_flags(uint32_t* flags) {
+  if (flags == nullptr) return SYEV3_EINVAL;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e);
+  unsigned v = 0;
+  e = syev3::take_flags_f64(&v);
+  if (e != cudaSuccess) return cuda_fail(e);
+  *flags = v;
+  return SYEV3_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+"""Thin ctypes binding of ``libsyev3.so`` (include/syev3.h).
+
+Argument marshalling only: tensors are passed to the C ABI as raw device
+pointers together with the current CUDA stream; every step of the solve runs
+in the library's kernels.  There is no CPU fallback -- a missing library or a
+CPU tensor raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsyev3.so")
+
+SYEV3_F64, SYEV3_F32, SYEV3_F32_COMPENSATED = 0, 1, 2
+SYEV3_OK, SYEV3_EINVAL, SYEV3_ECUDA, SYEV3_ENOCONV, SYEV3_ETIMEOUT = 0, 1, 2, 3, 4
+NUM_COUNTERS = 4
+
+_lock = threading.Lock()
+_lib = None
+
+
+class Syev3Error(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = _load()
+        msg = lib.syev3_status_string(status).decode()
+        if status == SYEV3_ECUDA:
+            msg += f" (cudaError {lib.syev3_last_cuda_error()})"
+        super().__init__(f"{where}: {msg}")
+        self.status = status
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is not built; run `python -m paper_1806_06698_gb300.build` "
+                                   "(or __graft_entry__.build()) -- there is no CPU fallback")
+            lib = ctypes.CDLL(LIB_PATH)
+            vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+            lib.syev3_abi_version.restype = i32
+            lib.syev3_status_string.argtypes = [i32]
+            lib.syev3_status_string.restype = ctypes.c_char_p
+            lib.syev3_last_cuda_error.restype = i32
+            lib.syev3_batched.argtypes = [vp, i64, vp, vp, i32, vp]
+            lib.syev3_batched.restype = i32
+            lib.syev3_batched_ex.argtypes = [vp, i64, vp, vp, i32, vp, vp]
+            lib.syev3_batched_ex.restype = i32
+            lib.syev3_device_flags.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
+            lib.syev3_device_flags.restype = i32
+            _lib = lib
+    return _lib
+
+
+def library():
+    """The loaded ctypes library (loads it on first use)."""
+    return _load()
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(status: int, where: str):
+    if status != SYEV3_OK:
+        raise Syev3Error(status, where)
+
+
+def dtype_code(dtype: torch.dtype, compensated: bool = False) -> int:
+    if dtype == torch.float64:
+        if compensated:
+            raise ValueError("the compensated path takes float32 inputs")
+        return SYEV3_F64
+    if dtype == torch.float32:
+        return SYEV3_F32_COMPENSATED if compensated else SYEV3_F32
+    raise ValueError(f"unsupported dtype {dtype}")
+
+
+def syev3_batched(A6: torch.Tensor, *, vectors: bool = True, compensated: bool = False,
+                  out: tuple[torch.Tensor, torch.Tensor | None] | None = None,
+                  counters: torch.Tensor | None = None, stream=None):
+    """Eigenvalues (n,3) ascending and eigenvectors (n,3,3) (columns) of the
+    packed symmetric matrices ``A6`` (n,6) on the GPU.  ``counters`` is an
+    optional uint64-sized (int64) device tensor of 4 entries the kernels add
+    to (see include/syev3.h)."""
+    if not A6.is_cuda:
+        raise ValueError("A6 must be a CUDA tensor (no CPU fallback)")
+    if A6.dim() != 2 or A6.shape[1] != 6 or not A6.is_contiguous():
+        raise ValueError("A6 must be a contiguous (n, 6) tensor")
+    n = A6.shape[0]
+    code = dtype_code(A6.dtype, compensated)
+    if out is None:
+        lam = torch.empty((n, 3), dtype=A6.dtype, device=A6.device)
+        U = torch.empty((n, 3, 3), dtype=A6.dtype, device=A6.device) if vectors else None
+    else:
+        lam, U = out
+    lib = _load()
+    if counters is None:
+        st = lib.syev3_batched(_ptr(A6), n, _ptr(lam), _ptr(U), code, _stream(stream))
+    else:
+        st = lib.syev3_batched_ex(_ptr(A6), n, _ptr(lam), _ptr(U), code, _ptr(counters), _stream(stream))
+    _check(st, "syev3_batched")
+    return lam, U
+
+
+def device_flags() -> int:
+    """Device-side status bits since the last call (bit 0: a wait timed out)."""
+    lib = _load()
+    v = ctypes.c_uint32(0)
+    _check(lib.syev3_device_flags(ctypes.byref(v)), "syev3_device_flags")
+    return int(v.value)

@@ -1,0 +1,67 @@
+"""The C ABI without a GPU: the library loads, exports every function the
+public header declares, and rejects bad arguments on the host before any
+CUDA call."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER_DIR = os.path.join(ROOT, "include")
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(HEADER_DIR)):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(HEADER_DIR, fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(syev3_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1806_06698_gb300 import build as b
+
+    b.build()
+    from paper_1806_06698_gb300 import syev3
+
+    return syev3.library()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("syev3_batched", "syev3_batched_ex", "syev3_abi_version"):
+        assert required in names, names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"libsyev3.so does not export {name}"
+
+
+def test_abi_version(lib):
+    assert lib.syev3_abi_version() == 1
+
+
+def test_host_side_argument_checks(lib):
+    from paper_1806_06698_gb300 import syev3
+
+    vp = ctypes.c_void_p
+    dummy = vp(4096)
+    # n < 0, bad dtype, NULL input or output: EINVAL before any CUDA call
+    assert lib.syev3_batched(dummy, -1, dummy, dummy, 0, None) == syev3.SYEV3_EINVAL
+    assert lib.syev3_batched(dummy, 4, dummy, dummy, 7, None) == syev3.SYEV3_EINVAL
+    assert lib.syev3_batched(None, 4, dummy, dummy, 0, None) == syev3.SYEV3_EINVAL
+    assert lib.syev3_batched(dummy, 4, None, dummy, 0, None) == syev3.SYEV3_EINVAL
+    # misaligned for the element type
+    assert lib.syev3_batched(vp(4097), 4, dummy, None, 0, None) == syev3.SYEV3_EINVAL
+    # overlapping input and output
+    assert lib.syev3_batched(vp(4096), 4, vp(4096 + 8), None, 0, None) == syev3.SYEV3_EINVAL
+    # n == 0 is a no-op
+    assert lib.syev3_batched(None, 0, None, None, 0, None) == syev3.SYEV3_OK
+    assert lib.syev3_status_string(syev3.SYEV3_EINVAL).startswith(b"SYEV3_EINVAL")

@@ -1,0 +1,157 @@
+"""FP64 parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bar (FP64): |dlambda| <= 8 eps ||A||_F per eigenvalue, residual <= 1e-14
+||A||_F, orthogonality <= 16 eps, eigenvectors (where the relative gap is
+>= 1e-6) within 32 eps / gap up to sign; exact diagonals bit for bit.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1806_06698_gb300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def syev3():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_06698_gb300 import build, syev3 as mod
+
+    build.build()
+    return mod
+
+
+def run_gpu(mod, A6_np, vectors=True, counters=None):
+    A = torch.from_numpy(np.ascontiguousarray(A6_np)).cuda()
+    lam, U = mod.syev3_batched(A, vectors=vectors, counters=counters)
+    torch.cuda.synchronize()
+    return lam.cpu().numpy(), (U.cpu().numpy() if U is not None else None)
+
+
+def test_gaussian_4096(syev3):
+    """The small parity workload: 4096 matrices with iid N(0,1) entries."""
+    A = inputs.gaussian(4096)
+    lam, U = run_gpu(syev3, A)
+    lam_o, U_o = oracle.syev3(A)
+    parity.compare_f64(A, lam, U, lam_o, U_o)
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 127, 128, 129, 1000, 3 * 128 + 37, 20011])
+def test_mixed_ragged(syev3, n):
+    """The mixed-difficulty recipe at sizes spanning several tiles and a ragged tail."""
+    A, ids = inputs.mixed(n, seed=1000 + n)
+    lam, U = run_gpu(syev3, A)
+    lam_o, U_o = oracle.syev3(A)
+    parity.compare_f64(A, lam, U, lam_o, U_o)
+
+
+def test_mixed_subsets_and_exact_diagonals(syev3):
+    A, ids = inputs.mixed(1 << 16, seed=77)
+    lam, U = run_gpu(syev3, A)
+    lam_o, U_o, info = oracle.syev3(A, with_info=True)
+    for s in inputs.SUBSET_NAMES:
+        m = ids == s
+        parity.compare_f64(A[m], lam[m], U[m], lam_o[m], U_o[m])
+    d = ids == inputs.SUBSET_DIAGONAL_REPEATED
+    assert np.array_equal(lam[d], lam_o[d]) and np.array_equal(U[d], U_o[d])
+
+
+def test_eigenvalues_only_matches(syev3):
+    A, _ = inputs.mixed(5000, seed=78)
+    lam_v, _ = run_gpu(syev3, A, vectors=True)
+    lam_n, U_n = run_gpu(syev3, A, vectors=False)
+    assert U_n is None
+    assert np.array_equal(lam_v, lam_n)
+
+
+def test_scale_equivariance_bitwise(syev3):
+    """Power-of-two scaling commutes with the solve bit for bit."""
+    A, _ = inputs.mixed(3000, seed=79, log10_scale=0.0)
+    lam0, U0 = run_gpu(syev3, A)
+    for k in (-500, -11, 7, 500):
+        lam, U = run_gpu(syev3, np.ldexp(A, k))
+        assert np.array_equal(lam, np.ldexp(lam0, k)) and np.array_equal(U, U0)
+
+
+def test_special_inputs_and_counters(syev3):
+    A = inputs.gaussian(300, seed=80)
+    A[0] = 0.0
+    A[1, 2] = np.nan
+    A[2, 4] = np.inf
+    A[3, 0] = -np.inf
+    ctr = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device="cuda")
+    lam, U = run_gpu(syev3, A, counters=ctr)
+    c = ctr.cpu().numpy()
+    assert c[1] == 3 and c[0] == 0
+    assert np.array_equal(lam[0], np.zeros(3)) and np.array_equal(U[0], np.eye(3))
+    assert np.all(np.isnan(lam[1:4])) and np.all(np.isnan(U[1:4]))
+    lam_o, U_o = oracle.syev3(A[4:])
+    parity.compare_f64(A[4:], lam[4:], U[4:], lam_o, U_o)
+
+
+def test_closed_forms(syev3):
+    import oracle_pins
+
+    cases = oracle_pins.load_closed_forms()
+    A = np.stack([c[1] for c in cases])
+    lam, U = run_gpu(syev3, A)
+    lam_o, U_o = oracle.syev3(A)
+    parity.compare_f64(A, lam, U, lam_o, U_o)
+
+
+def test_unaligned_buffers(syev3):
+    """8-byte but not 16-byte aligned buffers take the plain-load path."""
+    A, _ = inputs.mixed(777, seed=81)
+    buf = torch.zeros(777 * 6 + 1, dtype=torch.float64, device="cuda")
+    buf[1:] = torch.from_numpy(A.reshape(-1)).cuda()
+    A_view = buf[1:].view(777, 6)
+    lam_buf = torch.zeros(777 * 3 + 1, dtype=torch.float64, device="cuda")
+    U_buf = torch.zeros(777 * 9 + 1, dtype=torch.float64, device="cuda")
+    lam_v, U_v = lam_buf[1:].view(777, 3), U_buf[1:].view(777, 3, 3)
+    syev3.syev3_batched(A_view, out=(lam_v, U_v))
+    torch.cuda.synchronize()
+    lam_o, U_o = oracle.syev3(A)
+    parity.compare_f64(A, lam_v.cpu().numpy(), U_v.cpu().numpy(), lam_o, U_o)
+    assert lam_buf[0].item() == 0.0 and U_buf[0].item() == 0.0
+
+
+def test_rejects_bad_buffers(syev3):
+    A = torch.zeros(16, 6, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(16, 3, dtype=torch.float64, device="cuda")
+    lib = syev3.library()
+    import ctypes
+
+    host = np.zeros((16, 6))
+    st = lib.syev3_batched(ctypes.c_void_p(host.ctypes.data), 16, ctypes.c_void_p(lam.data_ptr()), None, 0, None)
+    assert st == syev3.SYEV3_EINVAL  # pageable host memory
+    st = lib.syev3_batched(ctypes.c_void_p(A.data_ptr() + 4), 15, ctypes.c_void_p(lam.data_ptr()), None, 0, None)
+    assert st == syev3.SYEV3_EINVAL  # 4-byte misaligned FP64
+
+
+def test_full_size_mixed_sampled(syev3):
+    """The 2^24 mixed FP64 batch in the benchmark's launch: every output is
+    checked for ordering, sign rule and orthogonality on the GPU, and 2^15
+    sampled matrices against the oracle one by one."""
+    n = 1 << 24
+    A, ids = inputs.mixed(n)
+    At = torch.from_numpy(A).cuda()
+    ctr = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device="cuda")
+    lam, U = syev3.syev3_batched(At, counters=ctr)
+    torch.cuda.synchronize()
+    assert ctr[0].item() == 0 and ctr[1].item() == 0
+    assert bool(torch.all(lam[:, 1:] >= lam[:, :-1]))
+    orth = torch.linalg.matrix_norm(U.transpose(1, 2) @ U - torch.eye(3, dtype=U.dtype, device=U.device))
+    assert float(orth.max()) <= 16 * parity.EPS64
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(n, 1 << 15, replace=False))
+    lam_s = lam[torch.from_numpy(idx).cuda()].cpu().numpy()
+    U_s = U[torch.from_numpy(idx).cuda()].cpu().numpy()
+    lam_o, U_o = oracle.syev3(A[idx])
+    parity.compare_f64(A[idx], lam_s, U_s, lam_o, U_o)
+    assert syev3.device_flags() == 0
