@@ -68,6 +68,7 @@ inline double val(Counted x) { return x.v; }
 // ---------------------------------------------------------------------------
 
 constexpr double EPS = DBL_EPSILON;  // reading: epsilon = 2^-52
+constexpr double kTinySpike = 0x1p-480; // reading: spikes below this are zeroed (see solve_one)
 
 struct Params {
   double c_defl = 1.0;    // reading: C in the deflation test of Sec. 1.1
@@ -323,6 +324,14 @@ void solve_one(const double ain[6], double lam_out[3], double U_out[9], const Pa
 
   // Sec. 1: ordered arrow.
   ArrowT<T> w = reduce_to_arrow(a);
+  // reading: a spike |beta_j| < 2^-480 of the pre-scaled arrow is set to
+  // zero -- an exact beta-deflation (Sec. 1.1) after a perturbation far
+  // below eps ||A|| -- so that beta_j^2, the products of the deflation test
+  // and those of the zero finder stay clear of underflow.  (Without it two
+  // tiny spikes make both sides of the test underflow to 0 <= 0 and
+  // "deflate" along an arbitrary direction.)
+  if (fabs(w.b1) < T(kTinySpike)) w.b1 = T(0.0);
+  if (fabs(w.b2) < T(kTinySpike)) w.b2 = T(0.0);
   const T a1 = w.a1, a2 = w.a2, b1 = w.b1, b2 = w.b2, g = w.g;
 
   T lamv[3];
@@ -350,9 +359,8 @@ void solve_one(const double ain[6], double lam_out[3], double U_out[9], const Pa
     else
       rhs = T(P.c_defl * EPS) * fabs(a1 + a2) * (h * h);
     // The "<=" takes the exact beta- and combo-deflations of Sec. 1.1
-    // (beta_j = 0 or alpha1 = alpha2 make the left side 0).  reading: a
-    // beta_j whose square underflows to 0 is a beta-deflation too.
-    if (lhs <= rhs || b1 * b1 == T(0.0) || b2 * b2 == T(0.0))
+    // (beta_j = 0 or alpha1 = alpha2 make the left side 0).
+    if (lhs <= rhs)
       cls = CLS_DEFLATED;
     else
       cls = CLS_REDUCED;
