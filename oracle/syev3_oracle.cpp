@@ -424,8 +424,16 @@ void solve_one(const double ain[6], double lam_out[3], double U_out[9], const Pa
         for (int i = 0; i < 3; ++i) tr->u[k][i] = val(V[k][i]);
     }
     // reading: normalise each vector by its 2-norm (Sec. 1.2 leaves them
-    // unnormalised; the outputs are to be orthonormal).
+    // unnormalised; the outputs are to be orthonormal).  The norm is taken
+    // of the vector scaled by the power of two that brings its largest
+    // component to [0.5, 1): exact, so nothing changes where no underflow
+    // occurs, while u2's degree-3 components (beta1 beta2 abar when mu and
+    // nu are both tiny) no longer underflow when squared.
     for (int k = 0; k < 3; ++k) {
+      double m = std::max(std::fabs(val(V[k][0])), std::max(std::fabs(val(V[k][1])), std::fabs(val(V[k][2]))));
+      int ev = 0;
+      if (m > 0.0) std::frexp(m, &ev);
+      for (int i = 0; i < 3; ++i) V[k][i] = T(std::ldexp(val(V[k][i]), -ev));
       T inv = T(1.0) / sqrt(V[k][0] * V[k][0] + V[k][1] * V[k][1] + V[k][2] * V[k][2]);
       for (int i = 0; i < 3; ++i) V[k][i] = V[k][i] * inv;
     }

@@ -74,7 +74,7 @@ def load_closed_forms():
             line = line.strip()
             if not line or line.startswith("#"):
                 continue
-            name, ent, lam, src = [t.strip() for t in line.split(";")]
+            name, ent, lam, src = [t.strip() for t in line.split(";", 3)]
             a_mp = [mp.mpf(eval(t, ns)) for t in ent.split()]
             a = np.array([float(v) for v in a_mp])
             for v, x in zip(a_mp, a):
