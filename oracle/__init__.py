@@ -28,7 +28,7 @@ _lib = None
 
 # Layout constants of oracle_trace (see syev3_oracle.cpp).
 TRACE_MAX = 72
-TRACE_LEN = 32 + 2 * 5 * TRACE_MAX
+TRACE_LEN = 32 + 2 * 6 * TRACE_MAX
 
 CLS_DIAGONAL, CLS_DEFLATED, CLS_REDUCED, CLS_NONFINITE = 0, 1, 2, 3
 
@@ -166,9 +166,9 @@ def trace(a6, **params) -> dict | None:
     T = TRACE_MAX
 
     def zf(off, nit):
-        blk = out[32 + off * 5 * T: 32 + (off + 1) * 5 * T].reshape(5, T)[:, :nit]
+        blk = out[32 + off * 6 * T: 32 + (off + 1) * 6 * T].reshape(6, T)[:, :nit]
         return dict(x=blk[0].copy(), f=blk[1].copy(), fp=blk[2].copy(),
-                    w0=blk[3].copy(), w1=blk[4].copy())
+                    w0=blk[3].copy(), w1=blk[4].copy(), direct=blk[5].astype(bool))
 
     r = dict(alpha1=out[0], alpha2=out[1], beta1=out[2], beta2=out[3], gamma=out[4],
              c=out[5], s=out[6], h=out[7], mu=out[8], nu=out[9],

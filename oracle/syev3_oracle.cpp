@@ -169,6 +169,7 @@ struct ZfTrace {
   double fp[kTraceMax];       // f'(x_j)
   double w0[kTraceMax];       // omega_0 at x_j (Sec. 1.4.1)
   double w1[kTraceMax];       // omega_1 at x_j (Sec. 1.4.1)
+  double direct[kTraceMax];   // 1 where x_{j+1} was taken directly as the zero of phi_j
 };
 
 struct ZfResult {
@@ -201,6 +202,7 @@ T bg_zero(T abar, T b1, T b2, T gbar, const Params& P, ZfResult* res, ZfTrace* t
       tr->w0[tr->n] = 1.0 + val(b2) * ab / ((xr + ab) * (xr + ab) * (xr + ab));
       double q = xr / (xr + ab);
       tr->w1[tr->n] = val(b1) + val(b2) * q * q * q;
+      tr->direct[tr->n] = 0.0;
       tr->n++;
     }
     // reading: an iterate at or left of the zero (f <= 0 can only come from
@@ -219,7 +221,22 @@ T bg_zero(T abar, T b1, T b2, T gbar, const Params& P, ZfResult* res, ZfTrace* t
     T disc = T(1.0) + (T(2.0) * a / b) * q;
     if (disc < T(0.0)) disc = T(0.0);  // reading: clamp a rounding-negative radicand
     T delta = q / (T(1.0) + sqrt(disc));
-    T xn = x - delta;
+    T xn;
+    if (delta < x * T(0.5)) {
+      xn = x - delta;
+    } else {
+      // reading: x_{j+1} is the zero of phi_j in (0, inf) (Sec. 1.4.1).  When
+      // it lies far below x_j, Delta agrees with x_j to many digits and
+      // x_j - Delta is rounding noise (it can even be negative), so the zero
+      // is taken directly from omega_0 x^2 - sigma x - omega_1 = 0, with
+      // omega_1 and sigma as in Sec. 1.4.1, in the form free of cancellation.
+      T xr = x * r2;
+      T w1 = b1 + b2 * xr * xr * xr;
+      T sigma = w0 * x - w1 * r1 - f;
+      T rt = sqrt(sigma * sigma + T(4.0) * w0 * w1);
+      xn = (sigma > T(0.0)) ? (sigma + rt) / (T(2.0) * w0) : (T(2.0) * w1) / (rt - sigma);
+      if (tr && tr->n > 0) tr->direct[tr->n - 1] = 1.0;
+    }
     // reading: a step that no longer decreases x means the iterate has
     // reached the rounding level of f; it is accepted.
     if (!(xn < x)) { converged = 1; break; }
@@ -251,6 +268,7 @@ T newton_zero(T abar, T b1, T b2, T gbar, const Params& P, ZfResult* res, ZfTrac
       tr->fp[tr->n] = val(fp);
       tr->w0[tr->n] = 0.0;
       tr->w1[tr->n] = 0.0;
+      tr->direct[tr->n] = 0.0;
       tr->n++;
     }
     // reading: an iterate at or right of the zero (f >= 0 can only come from
@@ -591,13 +609,13 @@ void oracle_count_ops(const double* A, int64_t n, uint64_t* ops, const double* p
 }
 
 // Internal quantities of one matrix, for the invariant tests.  Layout of out
-// (length >= 32 + 2 * 5 * 72):
+// (length >= 32 + 2 * 6 * 72):
 //  [0..7]   alpha1, alpha2, beta1, beta2, gamma, c, s, h   (scaled frame)
 //  [8..9]   mu, nu
 //  [10..18] u1, u2, u3 unnormalised (arrow frame)
 //  [19..23] class, it_mu, it_nu, converged, exponent
 //  [24]     n_mu (iterates traced), [25] n_nu
-//  [32 ...] mu trace: x[72], f[72], fp[72], w0[72], w1[72]; then the nu trace.
+//  [32 ...] mu trace: x[72], f[72], fp[72], w0[72], w1[72], direct[72]; then the nu trace.
 int oracle_trace(const double a[6], double* out, const double* params) {
   Params P = params_from(params);
   Trace tr;
@@ -614,7 +632,7 @@ int oracle_trace(const double a[6], double* out, const double* params) {
   out[24] = tr.zmu.n; out[25] = tr.znu.n;
   const ZfTrace* zs[2] = {&tr.zmu, &tr.znu};
   for (int z = 0; z < 2; ++z) {
-    double* o = out + 32 + z * 5 * kTraceMax;
+    double* o = out + 32 + z * 6 * kTraceMax;
     for (int j = 0; j < kTraceMax; ++j) {
       bool ok = j < zs[z]->n;
       o[j] = ok ? zs[z]->x[j] : 0.0;
@@ -622,6 +640,7 @@ int oracle_trace(const double a[6], double* out, const double* params) {
       o[2 * kTraceMax + j] = ok ? zs[z]->fp[j] : 0.0;
       o[3 * kTraceMax + j] = ok ? zs[z]->w0[j] : 0.0;
       o[4 * kTraceMax + j] = ok ? zs[z]->w1[j] : 0.0;
+      o[5 * kTraceMax + j] = ok ? zs[z]->direct[j] : 0.0;
     }
   }
   return inf.cls;

@@ -155,3 +155,38 @@ def test_full_size_mixed_sampled(syev3):
     lam_o, U_o = oracle.syev3(A[idx])
     parity.compare_f64(A[idx], lam_s, U_s, lam_o, U_o)
     assert syev3.device_flags() == 0
+
+
+@pytest.mark.parametrize("log2_spike", [-30, -60, -200, -400, -470, -490])
+def test_small_offdiagonal_scales(syev3, log2_spike):
+    """Off-diagonal entries 2^k below the diagonal: FP32 seeds stop being
+    usable (k <= -50), roots go to the compacted FP64 work list, and spikes
+    below 2^-480 are zeroed (beta-deflation)."""
+    A = inputs.gaussian(3000, seed=900 - log2_spike)
+    A[:, 3:] *= 2.0 ** log2_spike
+    lam, U = run_gpu(syev3, A)
+    lam_o, U_o = oracle.syev3(A)
+    parity.compare_f64(A, lam, U, lam_o, U_o)
+
+
+def test_entrywise_random_scales(syev3):
+    """Every entry with its own scale 2^U(-120, 0): all branches and both
+    zero-finder paths mixed in each warp."""
+    rng = np.random.default_rng(901)
+    A = rng.standard_normal((50000, 6)) * 2.0 ** rng.uniform(-120, 0, (50000, 6))
+    lam, U = run_gpu(syev3, A)
+    lam_o, U_o = oracle.syev3(A)
+    parity.compare_f64(A, lam, U, lam_o, U_o)
+
+
+def test_clustered_extremes(syev3):
+    """Q diag(1, 1+10^-k, -1) Q^T for k up to 15: mu is below FP32
+    resolution and is finished by the compacted FP64 iteration."""
+    rng = np.random.default_rng(902)
+    n = 20000
+    k = rng.uniform(6.0, 15.0, n)
+    d = np.stack([np.ones(n), 1.0 + 10.0 ** (-k), -np.ones(n)], axis=1)
+    A = inputs.conj_diag(inputs.haar(rng, n), d)
+    lam, U = run_gpu(syev3, A)
+    lam_o, U_o = oracle.syev3(A)
+    parity.compare_f64(A, lam, U, lam_o, U_o)

@@ -60,6 +60,8 @@ MUTANTS = [
     ("grad_mask_ignored", "C[i][j] = (std::fabs(gap) < tau * nrm) ? 0.0 : M[i][j] / gap;",
      "C[i][j] = M[i][j] / gap;"),
     ("newton_step_sign", "T xn = x - f / fp;", "T xn = x + f / fp;"),
+    ("direct_step_dropped", "if (delta < x * T(0.5)) {", "if (true) {"),
+    ("direct_step_sigma_sign", "T sigma = w0 * x - w1 * r1 - f;", "T sigma = w0 * x - w1 * r1 + f;"),
     ("norm_unscaled", "if (m > 0.0) std::frexp(m, &ev);", "(void)m;"),
     ("tiny_spike_rule_dropped", "constexpr double kTinySpike = 0x1p-480;", "constexpr double kTinySpike = 0.0;"),
 ]
