@@ -169,11 +169,13 @@ def test_small_offdiagonal_scales(syev3, log2_spike):
     parity.compare_f64(A, lam, U, lam_o, U_o)
 
 
-def test_entrywise_random_scales(syev3):
-    """Every entry with its own scale 2^U(-120, 0): all branches and both
-    zero-finder paths mixed in each warp."""
-    rng = np.random.default_rng(901)
-    A = rng.standard_normal((50000, 6)) * 2.0 ** rng.uniform(-120, 0, (50000, 6))
+@pytest.mark.parametrize("lo", [-120, -300])
+def test_entrywise_random_scales(syev3, lo):
+    """Every entry with its own scale 2^U(lo, 0): all branches, both
+    zero-finder paths and direct steps to far smaller zeros, mixed in each
+    warp."""
+    rng = np.random.default_rng(901 - lo)
+    A = rng.standard_normal((50000, 6)) * 2.0 ** rng.uniform(lo, 0, (50000, 6))
     lam, U = run_gpu(syev3, A)
     lam_o, U_o = oracle.syev3(A)
     parity.compare_f64(A, lam, U, lam_o, U_o)
@@ -189,4 +191,20 @@ def test_clustered_extremes(syev3):
     A = inputs.conj_diag(inputs.haar(rng, n), d)
     lam, U = run_gpu(syev3, A)
     lam_o, U_o = oracle.syev3(A)
+    parity.compare_f64(A, lam, U, lam_o, U_o)
+
+
+def test_near_combo_arrows(syev3):
+    """alpha1 - alpha2 = 10^U(-12,-2) with O(1) spikes (not deflated when
+    alpha1 + alpha2 is small): roots far above abar, where the spectral
+    function must be evaluated in the paper's printed form."""
+    rng = np.random.default_rng(903)
+    n = 20000
+    a1 = rng.uniform(-0.05, 0.05, n)
+    ab = 10.0 ** rng.uniform(-12, -2, n)
+    ang = rng.uniform(0.1, 1.4, n)
+    A = np.stack([a1, a1 - ab, rng.standard_normal(n), np.zeros(n), np.cos(ang), np.sin(ang)], axis=1)
+    lam, U = run_gpu(syev3, A)
+    lam_o, U_o, info = oracle.syev3(A, with_info=True)
+    assert (info[:, 0] == oracle.CLS_REDUCED).mean() > 0.5
     parity.compare_f64(A, lam, U, lam_o, U_o)
