@@ -37,7 +37,7 @@ BYTES_PER_MATRIX_F64 = 48 + 24 + 72  # packed input + eigenvalues + eigenvectors
 # Algorithmic FP64 operations per matrix of the mixed batch (add/sub + mul +
 # div + sqrt of the paper's method as the oracle's counting scalar executes
 # it, mean over the batch; tests/test_bench_constants.py re-derives it).
-FLOPS_PER_MATRIX_F64 = 289.0
+FLOPS_PER_MATRIX_F64 = 313.7
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz.
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -46,11 +46,12 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--steps", type=int, default=60)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["native", "reference"], default="native")
     p.add_argument("--n", type=int, default=N_MATRICES, help=argparse.SUPPRESS)
     p.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--fp64-only", action="store_true", help="skip the FP32 precision-form legs")
     return p.parse_args()
 
 
@@ -135,8 +136,8 @@ def cpu_baseline(A: np.ndarray, sample: int, seconds_hint: float = 0.0) -> dict:
     sub = np.ascontiguousarray(A[:sample])
     _, _, secs = oracle.syev3_timed(sub, cores)
     return {"value": sample / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {sample} matrices of the 2^24 mixed FP64 batch, std::thread over {cores} cores, "
-                      f"{secs:.2f} s wall"}
+            "sample": f"first {sample} matrices of the mixed FP64 batch, std::thread over {cores} cores, "
+                      f"{secs:.2f} s wall ({secs * cores:.1f} core-s)"}
 
 
 def run_reference(args):
@@ -173,6 +174,80 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _timed(step, steps: int, warmup: int, stream, barrier):
+    """Run ``warmup`` untimed then ``steps`` timed calls of ``step`` on
+    ``stream``; returns (total ms, per-launch ms) from CUDA events recorded on
+    that stream."""
+    import torch
+
+    for _ in range(warmup):
+        step()
+    barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(steps):
+        ev[2 * i].record(stream)
+        step()
+        ev[2 * i + 1].record(stream)
+    t1.record(stream)
+    barrier()
+    return t0.elapsed_time(t1), [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(steps)]
+
+
+def _fp32_legs(args, dev, stream, barrier, A64_dev):
+    """Precision form: the 2^24 mixed batch in FP32 (scale 10^U(-6,6)) and
+    2^26 FP32 structure tensors, plain FP32 and compensated, each timed like
+    the headline and checked against the FP64 kernel on a sample."""
+    import torch
+
+    from paper_1806_06698_gb300 import inputs, syev3
+
+    hbm = load_peaks().get("hbm_gbs", 6686.1)
+    out = {}
+    sets = [("mixed_fp32_2^24", inputs.mixed_fp32(args.n)[0]),
+            ("structure_tensors_fp32_2^26", inputs.structure_tensors(4 * args.n).astype(np.float32))]
+    for name, A_np in sets:
+        n = A_np.shape[0]
+        A = torch.from_numpy(A_np).to(dev)
+        lam = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        U = torch.empty((n, 3, 3), dtype=torch.float32, device=dev)
+        # FP64 solve of a sample of the same (upcast) matrices as the accuracy reference.
+        idx = torch.arange(0, n, max(1, n // (1 << 18)), device=dev)
+        A_ref = A[idx].double().contiguous()
+        lam_ref, _ = syev3.syev3_batched(A_ref, stream=stream)
+        nrm = torch.linalg.vector_norm(lam_ref, dim=1)
+        for mode in ("plain", "compensated"):
+            comp = mode == "compensated"
+            ctr = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device=dev)
+
+            def step():
+                syev3.syev3_batched(A, out=(lam, U), compensated=comp, stream=stream)
+
+            total_ms, kms = _timed(step, args.steps, args.warmup, stream, barrier)
+            syev3.syev3_batched(A, out=(lam, U), compensated=comp, counters=ctr, stream=stream)
+            barrier()
+            dl = ((lam[idx].double() - lam_ref).abs().amax(dim=1) / nrm.clamp_min(1e-300)).max().item()
+            orth = torch.linalg.matrix_norm(U[idx].double().transpose(1, 2) @ U[idx].double()
+                                            - torch.eye(3, dtype=torch.float64, device=dev)).max().item()
+            k = statistics.mean(kms)
+            gbs = 72 * n / (k * 1e-3) / 1e9
+            out[f"{name}_{mode}"] = {
+                "value": n * args.steps / (total_ms * 1e-3), "unit": UNIT, "ms_per_step": total_ms / args.steps,
+                "dtype": "f32", "n": n,
+                "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                             "traffic": None, "kernel": "k_syev3_f32", "peak_source": "MEASURED_PEAKS hbm_gbs"},
+                "fp64_refined_fraction": ctr[2].item() / n if comp else 0.0,
+                "max_dlambda_vs_fp64_kernel_eps32": dl / 2.0 ** -23,
+                "max_orthogonality_eps32": orth / 2.0 ** -23,
+                "accuracy_sample": int(idx.numel()),
+            }
+        del A, lam, U, A_ref
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_native(args):
     import torch
 
@@ -202,25 +277,10 @@ def run_native(args):
     def step():
         syev3.syev3_batched(A, out=(lam, U), stream=stream)
 
-    for _ in range(args.warmup):
-        step()
-    barrier()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
-    barrier()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for i in range(args.steps):
-        ev[2 * i].record(stream)
-        step()
-        ev[2 * i + 1].record(stream)
-    t1.record(stream)
-    barrier()
+    total_ms, kernel_ms = _timed(step, args.steps, args.warmup, stream, barrier)
     clocks = sampler.stop()
-    total_ms = t0.elapsed_time(t1)
-    kernel_ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps)]
     if ws > 1:
         t = torch.tensor([total_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -241,21 +301,14 @@ def run_native(args):
         lam_host.copy_(lam, non_blocking=True)
         U_host.copy_(U, non_blocking=True)
 
-    e2e_step()
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
-    e1.record(stream)
-    barrier()
-    e2e_ms = e0.elapsed_time(e1)
+    e2e_ms, _ = _timed(e2e_step, e2e_steps, 1, stream, barrier)
     if ws > 1:
         t = torch.tensor([e2e_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e_value = ws * n * e2e_steps / (e2e_ms * 1e-3)
+
+    fp32 = None if args.fp64_only else _fp32_legs(args, dev, stream, barrier, A)
 
     if rank == 0:
         kms = statistics.mean(kernel_ms)
@@ -263,6 +316,7 @@ def run_native(args):
         roofline = {"bound": "alu", "achieved": achieved / 1e3, "peak": FP64_PEAK_GFLOPS / 1e3,
                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
                     "kernel": "k_syev3_f64", "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                    "kernel_ms": kms,
                     "hbm_frac_of_measured": (BYTES_PER_MATRIX_F64 * n / (kms * 1e-3) / 1e9) /
                     load_peaks().get("hbm_gbs", 6686.1)}
         line = {
@@ -280,8 +334,10 @@ def run_native(args):
                     "d2h_bytes_per_step": n * 96},
             "clocks": clocks,
         }
+        if fp32 is not None:
+            line["precision_form"] = fp32
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(A_np, min(n, 1 << 22))
+            line["cpu_baseline"] = cpu_baseline(A_np, n)
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

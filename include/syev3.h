@@ -76,8 +76,8 @@ int syev3_last_cuda_error(void);
  *   stream    : CUDA stream the work is ordered on.
  * Returns SYEV3_EINVAL (NULL A or lambda, n < 0, bad dtype, misaligned or
  * overlapping buffers) or SYEV3_ECUDA (launch failure); SYEV3_OK otherwise.
- * The SYEV3_F32_COMPENSATED path needs scratch; this entry point takes it
- * from the stream-ordered allocator (cudaMallocAsync) of the current device.
+ * No entry point allocates device memory: the FP64 refinement of the
+ * compensated FP32 form works on a shared-memory list inside the kernel.
  */
 int syev3_batched(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype,
                   syev3_stream_t stream);
@@ -87,7 +87,8 @@ int syev3_batched(const void* A_packed6, int64_t n, void* lambda, void* U, int d
  *                [0] lanes whose zero finder hit the step cap,
  *                [1] lanes with a non-finite input entry,
  *                [2] lanes refined in FP64 (SYEV3_F32_COMPENSATED only),
- *                [3] reserved (0).
+ *                [3] refined lanes whose FP64 residual ||A u - lambda u||
+ *                    exceeded 16 eps32 ||A||_F (SYEV3_F32_COMPENSATED only).
  *                The caller zeroes them; they accumulate across calls.
  */
 int syev3_batched_ex(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype,

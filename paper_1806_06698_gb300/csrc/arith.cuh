@@ -1,0 +1,99 @@
+// arith.cuh -- arithmetic primitives of the eigensolver kernels (sm_103a).
+#pragma once
+
+#include <cstdint>
+
+namespace syev3 {
+namespace {  // internal linkage: every translation unit gets its own copy
+
+// 1/x: hardware estimate (relative error 2^-20) refined by one cubic
+// Newton-Raphson step, e = 1 - x y, y <- y (1 + e + e^2) (error e^3 ~ 2^-60);
+// within 1 ulp for 2^-1000 < |x| < 2^1000.
+__device__ __forceinline__ double rcp64(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+
+__device__ __forceinline__ float rcp32(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float sqrt32(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float rsqrt32(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// 2^k for -1022 <= k <= 1023, built from its exponent field.
+__device__ __forceinline__ double pow2(int k) { return __hiloint2double((k + 1023) << 20, 0); }
+
+// 2^k as a float for -126 <= k <= 127.
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: an unevaluated sum h + l of two floats, built on
+// the error-free transformations TwoSum (Knuth, TAOCP vol. 2, 4.2.2),
+// FastTwoSum (Dekker 1971, |a| >= |b|) and TwoProd via FMA.  These carry
+// about 48 bits, enough to evaluate a secular function or a deflation test
+// without the rounding of its FP32 products.
+// ---------------------------------------------------------------------------
+
+struct F2 {
+  float h, l;
+};
+
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ F2 two_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+
+__device__ __forceinline__ F2 ff_add(F2 x, F2 y) {
+  const F2 s = two_sum(x.h, y.h);
+  return fast_two_sum(s.h, s.l + (x.l + y.l));
+}
+
+__device__ __forceinline__ F2 ff_neg(F2 x) { return {-x.h, -x.l}; }
+
+__device__ __forceinline__ F2 ff_mul(F2 x, F2 y) {
+  const F2 p = two_prod(x.h, y.h);
+  return fast_two_sum(p.h, fmaf(x.h, y.l, fmaf(x.l, y.h, p.l)));
+}
+
+__device__ __forceinline__ F2 ff_mul1(F2 x, float y) {
+  const F2 p = two_prod(x.h, y);
+  return fast_two_sum(p.h, fmaf(x.l, y, p.l));
+}
+
+// x / y with one correction: q = x.h / y.h, remainder x - q y formed exactly
+// to first order, q + remainder / y.
+__device__ __forceinline__ F2 ff_div(F2 x, F2 y, float ry /* ~1/y.h */) {
+  const float q = x.h * ry;
+  const float r = (fmaf(-q, y.h, x.h) + x.l) - q * y.l;
+  return fast_two_sum(q, r * ry);
+}
+
+__device__ __forceinline__ bool ff_le(F2 x, F2 y) { return x.h < y.h || (x.h == y.h && x.l <= y.l); }
+
+}  // namespace
+}  // namespace syev3

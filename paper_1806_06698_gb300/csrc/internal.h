@@ -7,14 +7,18 @@
 namespace syev3 {
 
 // Counters layout (see syev3_batched_ex): [0] capped, [1] non-finite,
-// [2] refined in FP64, [3] reserved.
+// [2] refined in FP64, [3] refined lanes failing the FP64 residual check.
 constexpr int kNumCounters = 4;
 
 cudaError_t launch_f64(const double* A, int64_t n, double* lam, double* U, unsigned long long* counters,
                        cudaStream_t stream);
 
-// Reads and clears the __device__ status word of each translation unit
-// (synchronises the device).
+cudaError_t launch_f32(const float* A, int64_t n, float* lam, float* U, bool compensated,
+                       unsigned long long* counters, cudaStream_t stream);
+
+// Read and clear the __device__ status word of each translation unit
+// (synchronise the device).
 cudaError_t take_flags_f64(unsigned* flags);
+cudaError_t take_flags_f32(unsigned* flags);
 
 }  // namespace syev3

@@ -88,8 +88,13 @@ int syev3_batched_ex(const void* A_packed6, int64_t n, void* lambda, void* U, in
       e = syev3::launch_f64(static_cast<const double*>(A_packed6), n, static_cast<double*>(lambda),
                             static_cast<double*>(U), ctr, s);
       break;
+    case SYEV3_F32:
+    case SYEV3_F32_COMPENSATED:
+      e = syev3::launch_f32(static_cast<const float*>(A_packed6), n, static_cast<float*>(lambda),
+                            static_cast<float*>(U), dtype == SYEV3_F32_COMPENSATED, ctr, s);
+      break;
     default:
-      return SYEV3_EINVAL;  // FP32 paths are added by their own translation units
+      return SYEV3_EINVAL;
   }
   return e == cudaSuccess ? SYEV3_OK : cuda_fail(e);
 }
@@ -104,6 +109,7 @@ int syev3_device_flags(uint32_t* flags) {
   if (e != cudaSuccess) return cuda_fail(e);
   unsigned v = 0;
   e = syev3::take_flags_f64(&v);
+  if (e == cudaSuccess) e = syev3::take_flags_f32(&v);
   if (e != cudaSuccess) return cuda_fail(e);
   *flags = v;
   return SYEV3_OK;

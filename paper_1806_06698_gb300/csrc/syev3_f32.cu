@@ -1,0 +1,610 @@
+// syev3_f32.cu -- FP32 batched 3x3 symmetric eigensolver for sm_103a, plain
+// and compensated (the precision form).
+//
+// The steps are those of the FP64 solver (C. F. Borges, arXiv 1806.06698,
+// Secs. 1-1.4.1) carried out in FP32: ordered Jacobi rotation to an arrow,
+// the deflation test, the deflated 2x2 solve or the Borges-Gragg zero finder
+// for mu and nu, the trace identity and the closed-form eigenvectors.  The
+// spectral function is evaluated in the cancellation-free form for x < abar
+// (see solve_f64.cuh).
+//
+// The compensated form (SYEV3_F32_COMPENSATED) adds, in FP32:
+//  * double-float (error-free transformation) products in the deflation
+//    test of Sec. 1.1, so the decision is not blurred by FP32 rounding;
+//  * a double-float evaluation of the spectral function at the FP32 root
+//    and one Newton correction (Sec. 1.4.2) with it;
+// and uses FP64 only on the lanes it flags -- near-deflated (the test's two
+// sides within a factor kNearDefl), clustered (a relative eigenvalue gap
+// below kClusterTau) or capped -- for a final FP64 Newton step on mu and nu,
+// eigenvectors re-formed (and so re-orthogonalised) in FP64 and an FP64
+// residual check against the input.  Flagged lanes are compacted with warp
+// ballots into a shared-memory list so the FP64 work runs on as few warps as
+// possible; no global scratch memory is used.
+//
+// Memory path as in the FP64 kernel: tiles of kTPB records (24 B each) by
+// 1-D bulk copy into shared memory, double-buffered on mbarriers; results
+// staged in shared memory and written with 16-byte stores.  The plain form
+// moves 72 B per matrix and is bound by HBM bandwidth.
+
+#include <cmath>
+#include <cstdint>
+
+#include "common.cuh"
+#include "internal.h"
+#include "solve_f64.cuh"
+
+namespace syev3 {
+namespace {
+
+constexpr int kTPB = 128;
+constexpr int kMaxIt32 = 32;              // FP32 zero-finder step cap
+constexpr float kEps32 = 0x1p-23f;
+constexpr float kCDefl32 = 1.0f;          // C of the deflation test (Sec. 1.1)
+constexpr float kCTerm32 = 2.0f;          // C of the stopping rule (Sec. 1.4.1)
+constexpr float kTinySpike32 = 0x1p-60f;  // spikes below this are zeroed (beta-deflation)
+constexpr float kNearDefl = 16.0f;        // near-deflated: test sides within this factor
+constexpr float kClusterTau = 0x1p-16f;   // clustered: relative gap below this
+constexpr double kResidualTol = 16.0 * 0x1p-23;  // FP64 residual check, times ||A||_F
+
+constexpr int kDiag = f64::kDiagonal, kDefl = f64::kDeflated, kRed = f64::kReduced,
+              kNonFin = f64::kNonFinite, kIdle = f64::kIdle;
+
+__device__ unsigned g_flags32;
+
+struct Lane32 {
+  float a1, a2, b1, b2, g, c, s;  // ordered arrow and rotation (pre-scaled frame)
+  int e;                          // A was divided by 2^e
+  int cls;
+  bool near_defl;
+};
+
+// Sec. 1: ordered Jacobi rotation of [[p,q],[q,r]] in FP32.
+struct Rot32 {
+  float c, s, l1, l2;
+};
+
+__device__ __forceinline__ Rot32 ordered_rotation32(float p, float q, float r) {
+  Rot32 J;
+  if (q == 0.f) {
+    const bool keep = p >= r;
+    J.c = keep ? 1.f : 0.f;
+    J.s = keep ? 0.f : 1.f;
+    J.l1 = keep ? p : r;
+    J.l2 = keep ? r : p;
+    return J;
+  }
+  const float D = p - r, q2 = q + q;
+  const float rad = sqrt32(fmaf(D, D, q2 * q2));
+  const float den = fabsf(D) + rad;
+  const float t = (den > 0.f) ? q2 * rcp32(den) : copysignf(1.f, q);
+  const bool right = D >= 0.f;
+  const float hi = right ? p : r, lo = right ? r : p;
+  J.l1 = fmaf(t, q, hi);
+  J.l2 = fmaf(-t, q, lo);
+  const float k = rsqrt32(fmaf(t, t, 1.f));
+  J.c = right ? k : t * k;
+  J.s = right ? t * k : k;
+  return J;
+}
+
+template <bool kComp>
+__device__ __forceinline__ Lane32 make_lane32(const float a_in[6]) {
+  Lane32 L;
+  L.near_defl = false;
+  int E = 0;
+  bool finite = true;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const int ex = (__float_as_int(a_in[i]) >> 23) & 0xff;
+    finite &= (ex != 0xff);
+    E = max(E, ex);
+  }
+  if (!finite) {
+    L.cls = kNonFin;
+    return L;
+  }
+  float a[6];
+  if (E >= 1 && E <= 252) {  // exact power-of-two pre-scale: largest entry in [0.5, 1)
+    L.e = E - 126;
+    const float sc = pow2f(-L.e);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) a[i] = a_in[i] * sc;
+  } else {
+    float amax = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) amax = fmaxf(amax, fabsf(a_in[i]));
+    int e = 0;
+    if (amax > 0.f) frexpf(amax, &e);
+    L.e = e;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) a[i] = scalbnf(a_in[i], -e);
+  }
+  const Rot32 J = ordered_rotation32(a[0], a[3], a[1]);
+  L.a1 = J.l1;
+  L.a2 = J.l2;
+  L.c = J.c;
+  L.s = J.s;
+  L.g = a[2];
+  float b1 = fmaf(J.c, a[4], J.s * a[5]);
+  float b2 = fmaf(J.c, a[5], -J.s * a[4]);
+  if (fabsf(b1) < kTinySpike32) b1 = 0.f;
+  if (fabsf(b2) < kTinySpike32) b2 = 0.f;
+  L.b1 = b1;
+  L.b2 = b2;
+  if (b1 == 0.f && b2 == 0.f) {
+    L.cls = kDiag;
+    return L;
+  }
+  // Sec. 1.1: |abar b1 b2| <= C eps |a1 + a2| h^2.
+  if (kComp) {
+    // Double-float products: the decision sees the exact sides to ~2^-46.
+    const F2 ab = two_sum(L.a1, -L.a2);
+    const F2 lhs = ff_mul1(ff_mul1(ab, b1), b2);
+    const F2 sum12 = two_sum(L.a1, L.a2);
+    const F2 h2 = ff_add(two_prod(b1, b1), two_prod(b2, b2));
+    F2 rhs = ff_mul(sum12, h2);
+    rhs.h *= kCDefl32 * kEps32;
+    rhs.l *= kCDefl32 * kEps32;
+    const F2 al = {fabsf(lhs.h), lhs.h < 0.f ? -lhs.l : lhs.l};
+    const F2 ar = {fabsf(rhs.h), rhs.h < 0.f ? -rhs.l : rhs.l};
+    L.cls = ff_le(al, ar) ? kDefl : kRed;
+    L.near_defl = (al.h < kNearDefl * ar.h) && (al.h * kNearDefl > ar.h);
+  } else {
+    const float h2 = fmaf(b1, b1, b2 * b2);
+    const float lhs = fabsf((L.a1 - L.a2) * b1 * b2);
+    const float rhs = (kCDefl32 * kEps32) * fabsf(L.a1 + L.a2) * h2;
+    L.cls = (lhs <= rhs) ? kDefl : kRed;
+  }
+  return L;
+}
+
+// Borges-Gragg in FP32 for mu and nu together (Sec. 1.4.1), started from the
+// zero of Eq. (7); stops when f/f' < C eps32 x, when f <= 0 or when a step no
+// longer moves x.  For x < ab, f = x + K - b1/x + c x/(x+ab).
+__device__ __forceinline__ void roots32(const float ab, const float b1[2], const float b2[2], const float g[2],
+                                        const float c[2], const float K[2], float x[2], bool& capped) {
+  bool live[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float hg = 0.5f * g[k], bs = b1[k] + b2[k];
+    const float rt = sqrt32(fmaf(hg, hg, bs));
+    x[k] = (g[k] >= 0.f) ? hg + rt : bs * rcp32(rt - hg);
+    live[k] = true;
+  }
+  capped = false;
+#pragma unroll 1
+  for (int it = 0; it <= kMaxIt32 && (live[0] || live[1]); ++it) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (!live[k]) continue;
+      const float r1 = rcp32(x[k]), r2 = rcp32(x[k] + ab);
+      const float t1 = b1[k] * r1, t2 = b2[k] * r2;
+      const bool small = x[k] < ab;
+      const float f = ((x[k] + (small ? K[k] : -g[k])) - t1) + (small ? c[k] * x[k] * r2 : -t2);
+      const float fp = fmaf(t2, r2, fmaf(t1, r1, 1.f));
+      if (!(f > 0.f) || f < (kCTerm32 * kEps32) * x[k] * fp) {
+        live[k] = false;
+        continue;
+      }
+      if (it == kMaxIt32) {
+        capped = true;
+        live[k] = false;
+        continue;
+      }
+      const float w0 = fmaf(t2 * ab, r2 * r2, 1.f);
+      const float rb = rcp32(fmaf(f, r1, fp));
+      const float fr = f * rb;
+      const float z = (-4.f * w0) * (r1 * rb) * fr;
+      const float delta = 2.f * fr * rcp32(1.f + sqrt32(fmaxf(0.f, 1.f + z)));
+      float xn;
+      if (delta < 0.5f * x[k]) {
+        xn = x[k] - delta;
+      } else {  // the zero of phi_j directly (see the FP64 solver)
+        const float xr = x[k] * r2;
+        const float w1 = fmaf(b2[k] * xr, xr * xr, b1[k]);
+        const float sg = fmaf(w0, x[k], -fmaf(w1, r1, f));
+        const float rt = sqrt32(fmaf(sg, sg, 4.f * w0 * w1));
+        xn = (sg > 0.f) ? (sg + rt) * rcp32(2.f * w0) : (2.f * w1) * rcp32(rt - sg);
+      }
+      if (!(xn < x[k])) {
+        live[k] = false;
+        continue;
+      }
+      x[k] = xn;
+    }
+  }
+}
+
+// Double-float value of the spectral function at x (FP32 data exact), and
+// one Newton correction x - f/f' with it (Sec. 1.4.2).
+__device__ __forceinline__ float newton_ff(const F2 ab, const F2 b1, const F2 b2, const F2 g, const F2 c, const F2 K,
+                                          const float x) {
+  const float r1 = rcp32(x);
+  const F2 s = ff_add(two_sum(x, ab.h), {ab.l, 0.f});  // x + ab
+  const float r2 = rcp32(s.h);
+  const F2 xf = {x, 0.f};
+  const F2 t1 = ff_div(b1, xf, r1);
+  const bool small = x < ab.h;
+  F2 acc = ff_add(xf, small ? K : ff_neg(g));
+  acc = ff_add(acc, ff_neg(t1));
+  const F2 last = small ? ff_div(ff_mul1(c, x), s, r2) : ff_neg(ff_div(b2, s, r2));
+  acc = ff_add(acc, last);
+  const float f = acc.h + acc.l;
+  const float t1h = t1.h, t2h = b2.h * r2;
+  const float fp = fmaf(t2h, r2, fmaf(t1h, r1, 1.f));
+  const float xn = x - f * rcp32(fp);
+  return (xn > 0.f) ? xn : x;
+}
+
+// Eigenpairs of a classified lane in FP32 (scaled frame); returns eigenvalues
+// ascending in l[] and vectors as columns in U[i*3+k].
+__device__ __forceinline__ void finish32(const Lane32& L, float mu, float nu, float l_out[3], float U[9]) {
+  const float a1 = L.a1, a2 = L.a2, b1 = L.b1, b2 = L.b2, g = L.g;
+  float l[3], v[3][3];
+  if (L.cls == kDiag) {
+    l[0] = a1; l[1] = a2; l[2] = g;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) v[k][i] = (i == k) ? 1.f : 0.f;
+  } else if (L.cls == kDefl) {
+    const float h2 = fmaf(b1, b1, b2 * b2);
+    const float rh = rsqrt32(h2), h = h2 * rh;
+    const float gs = b1 * rh, gc = b2 * rh;
+    l[0] = fmaf(a1 * gc, gc, a2 * gs * gs);
+    v[0][0] = gc; v[0][1] = -gs; v[0][2] = 0.f;
+    const float d2 = fmaf(a1 * gs, gs, a2 * gc * gc);
+    const Rot32 K = ordered_rotation32(d2, h, g);
+    l[1] = K.l1; l[2] = K.l2;
+    v[1][0] = gs * K.c;  v[1][1] = gc * K.c;  v[1][2] = K.s;
+    v[2][0] = -gs * K.s; v[2][1] = -gc * K.s; v[2][2] = K.c;
+  } else {
+    const float abar = a1 - a2;
+    l[0] = a1 + mu;
+    l[1] = (nu - mu) + g;
+    l[2] = a2 - nu;
+    const float mpa = mu + abar, npa = nu + abar;
+    v[0][0] = b1 * mpa;         v[0][1] = b2 * mu;         v[0][2] = mu * mpa;
+    v[1][0] = -(b2 * mu) * npa; v[1][1] = (b1 * nu) * mpa; v[1][2] = (b1 * b2) * abar;
+    v[2][0] = b1 * nu;          v[2][1] = b2 * npa;        v[2][2] = -(nu * npa);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float ss = fmaf(v[k][0], v[k][0], fmaf(v[k][1], v[k][1], v[k][2] * v[k][2]));
+      if (!(ss >= 0x1p-100f)) {  // squares near underflow: exact power-of-two rescale
+        int E = 1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) E = max(E, (__float_as_int(v[k][i]) >> 23) & 0xff);
+        const float sc = pow2f(126 - E);
+        v[k][0] *= sc; v[k][1] *= sc; v[k][2] *= sc;
+        ss = fmaf(v[k][0], v[k][0], fmaf(v[k][1], v[k][1], v[k][2] * v[k][2]));
+      }
+      const float inv = rsqrt32(ss);
+      v[k][0] *= inv; v[k][1] *= inv; v[k][2] *= inv;
+    }
+  }
+  float x[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    x[k][0] = fmaf(L.c, v[k][0], -L.s * v[k][1]);
+    x[k][1] = fmaf(L.s, v[k][0], L.c * v[k][1]);
+    x[k][2] = v[k][2];
+  }
+  float l0 = l[0], l1 = l[1], l2 = l[2];
+  float x00 = x[0][0], x01 = x[0][1], x02 = x[0][2];
+  float x10 = x[1][0], x11 = x[1][1], x12 = x[1][2];
+  float x20 = x[2][0], x21 = x[2][1], x22 = x[2][2];
+#define SYEV3_CSWAP32(la, a0, a1_, a2_, lb, b0, b1_, b2_) \
+  if (lb < la) {                                         \
+    float t_;                                            \
+    t_ = la; la = lb; lb = t_;                           \
+    t_ = a0; a0 = b0; b0 = t_;                           \
+    t_ = a1_; a1_ = b1_; b1_ = t_;                       \
+    t_ = a2_; a2_ = b2_; b2_ = t_;                       \
+  }
+  SYEV3_CSWAP32(l0, x00, x01, x02, l1, x10, x11, x12)
+  SYEV3_CSWAP32(l1, x10, x11, x12, l2, x20, x21, x22)
+  SYEV3_CSWAP32(l0, x00, x01, x02, l1, x10, x11, x12)
+#undef SYEV3_CSWAP32
+  const float ls[3] = {l0, l1, l2};
+  const float xs[3][3] = {{x00, x01, x02}, {x10, x11, x12}, {x20, x21, x22}};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float y0 = xs[k][0], y1 = xs[k][1], y2 = xs[k][2];
+    float big = y0;
+    if (fabsf(y1) > fabsf(big)) big = y1;
+    if (fabsf(y2) > fabsf(y0) && fabsf(y2) > fabsf(y1)) big = y2;
+    const float sg = (big < 0.f) ? -1.f : 1.f;
+    l_out[k] = ls[k];
+    U[0 * 3 + k] = sg * y0;
+    U[1 * 3 + k] = sg * y1;
+    U[2 * 3 + k] = sg * y2;
+  }
+}
+
+__device__ __forceinline__ float unscale32(float v, int e) {
+  return (e >= -126 && e <= 127) ? v * pow2f(e) : scalbnf(v, e);
+}
+
+template <bool kBulkIn, bool kComp>
+__global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A, int64_t n,
+                                                    float* __restrict__ lam_out, float* __restrict__ U_out,
+                                                    unsigned long long* __restrict__ counters) {
+  __shared__ alignas(16) float s_in[2][kTPB * 6];
+  __shared__ alignas(16) float s_lam[kTPB * 3];
+  __shared__ alignas(16) float s_U[kTPB * 9];
+  // Compensated form: flagged lanes for the FP64 refinement (arrow, roots, owner).
+  __shared__ float s_fa[kComp ? 9 * kTPB : 1];
+  __shared__ int s_fi[kComp ? 2 * kTPB : 1];
+  __shared__ int s_nflag;
+  __shared__ alignas(8) uint64_t s_bar[2];
+
+  const int tid = threadIdx.x, lane_id = tid & 31;
+  const unsigned lt_mask = (1u << lane_id) - 1u;
+  const int64_t n_tiles = (n + kTPB - 1) / kTPB;
+  const bool want_U = (U_out != nullptr);
+  const bool vec_lam = ((reinterpret_cast<uintptr_t>(lam_out) & 15) == 0);
+  const bool vec_U = want_U && ((reinterpret_cast<uintptr_t>(U_out) & 15) == 0);
+
+  if (tid == 0) {
+    s_nflag = 0;
+    if (kBulkIn) {
+      mbar_init(&s_bar[0], 1);
+      mbar_init(&s_bar[1], 1);
+      fence_mbar_init();
+    }
+  }
+  __syncthreads();
+
+  // Bulk-copy part of a tile: its first (cnt * 24) & ~15 bytes; the odd last
+  // record of a tile with an odd count (8 bytes past a 16-byte boundary) is
+  // loaded with plain loads after the wait.
+  auto issue = [&](int64_t tile, int buf) {
+    const int64_t base = tile * kTPB;
+    const int cnt = (int)((n - base) < kTPB ? (n - base) : kTPB);
+    const uint32_t bytes = ((uint32_t)cnt * 24u) & ~15u;
+    mbar_arrive_expect_tx(&s_bar[buf], bytes);
+    if (bytes) bulk_g2s(s_in[buf], A + base * 6, bytes, &s_bar[buf]);
+  };
+
+  uint32_t phases = 0u;
+  int buf = 0;
+  int64_t tile = blockIdx.x;
+  if (kBulkIn && tid == 0 && tile < n_tiles) issue(tile, 0);
+
+  for (; tile < n_tiles; tile += gridDim.x, buf ^= 1) {
+    const int64_t base = tile * kTPB;
+    const int cnt = (int)((n - base) < kTPB ? (n - base) : kTPB);
+    const int64_t next = tile + gridDim.x;
+    if (kBulkIn) {
+      if (tid == 0 && next < n_tiles) issue(next, buf ^ 1);
+      const bool ok = mbar_wait(&s_bar[buf], (phases >> buf) & 1u);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(&g_flags32, kFlagWaitTimeout);
+        mbar_wait(&s_bar[buf], (phases >> buf) & 1u);
+        if (next < n_tiles) mbar_wait(&s_bar[buf ^ 1], (phases >> (buf ^ 1)) & 1u);
+        return;
+      }
+      phases ^= 1u << buf;
+      const int done_f = (int)((((uint32_t)cnt * 24u) & ~15u) / 4u);
+      for (int i = done_f + tid; i < cnt * 6; i += kTPB) s_in[buf][i] = A[base * 6 + i];
+      if (done_f < cnt * 6) __syncthreads();
+    } else {
+      for (int i = tid; i < cnt * 6; i += kTPB) s_in[buf][i] = A[base * 6 + i];
+      __syncthreads();
+    }
+
+    Lane32 L;
+    L.cls = kIdle;
+    L.near_defl = false;
+    float a_in[6];
+    if (tid < cnt) {
+      const float2* src = reinterpret_cast<const float2*>(&s_in[buf][tid * 6]);
+      const float2 p0 = src[0], p1 = src[1], p2 = src[2];
+      a_in[0] = p0.x; a_in[1] = p0.y; a_in[2] = p1.x; a_in[3] = p1.y; a_in[4] = p2.x; a_in[5] = p2.y;
+      L = make_lane32<kComp>(a_in);
+    }
+
+    // Roots (Sec. 1.2): problem 0 is mu, problem 1 is nu (spikes swapped).
+    float root[2] = {0.f, 0.f};
+    bool capped = false;
+    if (L.cls == kRed) {
+      const float ab = L.a1 - L.a2;
+      const float bb1 = L.b1 * L.b1, bb2 = L.b2 * L.b2;
+      const float pb1[2] = {bb1, bb2}, pb2[2] = {bb2, bb1};
+      const float pg[2] = {L.g - L.a1, L.a2 - L.g};
+      const float rab = rcp32(ab);
+      const float pc[2] = {pb2[0] * rab, pb2[1] * rab};
+      const float pK[2] = {-pg[0] - pc[0], -pg[1] - pc[1]};
+      roots32(ab, pb1, pb2, pg, pc, pK, root, capped);
+      if (kComp) {
+        // Exact FP32 data as double-float, then one Newton correction with
+        // a double-float f at each root.
+        const F2 abf = two_sum(L.a1, -L.a2);
+        const float rabh = rcp32(abf.h);
+        const F2 fb1 = two_prod(L.b1, L.b1), fb2 = two_prod(L.b2, L.b2);
+        const F2 fg0 = two_sum(L.g, -L.a1), fg1 = two_sum(L.a2, -L.g);
+        const F2 fc0 = ff_div(fb2, abf, rabh), fc1 = ff_div(fb1, abf, rabh);
+        const F2 fK0 = ff_neg(ff_add(fg0, fc0)), fK1 = ff_neg(ff_add(fg1, fc1));
+        root[0] = newton_ff(abf, fb1, fb2, fg0, fc0, fK0, root[0]);
+        root[1] = newton_ff(abf, fb2, fb1, fg1, fc1, fK1, root[1]);
+      }
+    }
+
+    bool flagged = false, nonfinite = false;
+    if (L.cls != kIdle) {
+      float l[3], U[9];
+      if (L.cls == kNonFin) {
+        nonfinite = true;
+        const float qnan = __int_as_float(0x7fc00000);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) l[k] = qnan;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) U[k] = qnan;
+      } else {
+        finish32(L, root[0], root[1], l, U);
+        if (kComp && L.cls != kDiag) {
+          const float nrm2 = fmaf(l[0], l[0], fmaf(l[1], l[1], l[2] * l[2]));
+          const float gap = fminf(l[1] - l[0], l[2] - l[1]);
+          flagged = capped || L.near_defl || (gap * gap < (kClusterTau * kClusterTau) * nrm2);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) l[k] = unscale32(l[k], L.e);
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) s_lam[tid * 3 + k] = l[k];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) s_U[tid * 9 + k] = U[k];
+    }
+
+    if (kComp) {
+      // Compact the flagged lanes and refine them in FP64 with every lane of
+      // the CTA available.
+      const unsigned m = __ballot_sync(0xffffffffu, flagged);
+      int wbase = 0;
+      if (lane_id == 0 && m) wbase = atomicAdd(&s_nflag, __popc(m));
+      wbase = __shfl_sync(0xffffffffu, wbase, 0);
+      if (flagged) {
+        const int slot = wbase + __popc(m & lt_mask);
+        float* f = &s_fa[slot * 9];
+        f[0] = L.a1; f[1] = L.a2; f[2] = L.b1; f[3] = L.b2; f[4] = L.g; f[5] = L.c; f[6] = L.s;
+        f[7] = root[0]; f[8] = root[1];
+        s_fi[slot * 2] = tid;
+        s_fi[slot * 2 + 1] = (L.e << 2) | L.cls;
+      }
+      __syncthreads();
+      const int nf = s_nflag;
+      for (int i = tid; i < nf; i += kTPB) {
+        const float* f = &s_fa[i * 9];
+        const int owner = s_fi[i * 2], code = s_fi[i * 2 + 1];
+        f64::Lane D;
+        D.a1 = f[0]; D.a2 = f[1]; D.b1 = f[2]; D.b2 = f[3]; D.g = f[4]; D.c = f[5]; D.s = f[6];
+        D.cls = code & 3;
+        D.e = code >> 2;
+        D.unscale = (D.e >= -1022 && D.e <= 1023) ? pow2(D.e) : 0.0;
+        double mu = f[7], nu = f[8];
+        if (D.cls == kRed) {
+          // Final FP64 Newton step on mu and nu (Sec. 1.4.2).
+          const double ab = D.a1 - D.a2, bb1 = D.b1 * D.b1, bb2 = D.b2 * D.b2;
+          const double rab = rcp64(ab);
+          const double g0 = D.g - D.a1, g1 = D.a2 - D.g;
+          const double c0 = bb2 * rab, c1 = bb1 * rab;
+          if (mu > 0.0) mu = f64::newton64(ab, bb1, bb2, g0, c0, -g0 - c0, mu);
+          if (nu > 0.0) nu = f64::newton64(ab, bb2, bb1, g1, c1, -g1 - c1, nu);
+        }
+        double lam[3], U[9];
+        f64::finish_lane(D, mu, nu, lam, U);  // eigenvectors re-formed in FP64
+        // FP64 residual check against the input record.
+        const float* rec = &s_in[buf][owner * 6];
+        const double M[3][3] = {{rec[0], rec[3], rec[4]}, {rec[3], rec[1], rec[5]}, {rec[4], rec[5], rec[2]}};
+        double nA = 0.0, worst = 0.0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) nA = fma(M[r][q], M[r][q], nA);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          double rr = 0.0;
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            const double v = fma(M[r][0], U[k], fma(M[r][1], U[3 + k], fma(M[r][2], U[6 + k], -lam[k] * U[r * 3 + k])));
+            rr = fma(v, v, rr);
+          }
+          worst = fmax(worst, rr);
+        }
+        if (counters != nullptr && !(worst <= kResidualTol * kResidualTol * nA)) atomicAdd(&counters[3], 1ull);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s_lam[owner * 3 + k] = (float)lam[k];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) s_U[owner * 9 + k] = (float)U[k];
+      }
+    }
+    if (counters != nullptr) {
+      const unsigned cm = __ballot_sync(0xffffffffu, capped);
+      const unsigned nf = __ballot_sync(0xffffffffu, nonfinite);
+      const unsigned fl = __ballot_sync(0xffffffffu, flagged);
+      if (lane_id == 0) {
+        if (cm) atomicAdd(&counters[0], (unsigned long long)__popc(cm));
+        if (nf) atomicAdd(&counters[1], (unsigned long long)__popc(nf));
+        if (fl) atomicAdd(&counters[2], (unsigned long long)__popc(fl));
+      }
+    }
+    __syncthreads();
+    if (tid == 0) s_nflag = 0;
+
+    {
+      float* dst = lam_out + base * 3;
+      const int m = cnt * 3;
+      if (vec_lam) {
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        const float4* s4 = reinterpret_cast<const float4*>(s_lam);
+        for (int i = tid; i < m / 4; i += kTPB) d4[i] = s4[i];
+        for (int i = (m & ~3) + tid; i < m; i += kTPB) dst[i] = s_lam[i];
+      } else {
+        for (int i = tid; i < m; i += kTPB) dst[i] = s_lam[i];
+      }
+    }
+    if (want_U) {
+      float* dst = U_out + base * 9;
+      const int m = cnt * 9;
+      if (vec_U) {
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        const float4* s4 = reinterpret_cast<const float4*>(s_U);
+        for (int i = tid; i < m / 4; i += kTPB) d4[i] = s4[i];
+        for (int i = (m & ~3) + tid; i < m; i += kTPB) dst[i] = s_U[i];
+      } else {
+        for (int i = tid; i < m; i += kTPB) dst[i] = s_U[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <bool kBulkIn, bool kComp>
+int blocks_per_sm_f32() {
+  static int cached = -1;
+  if (cached < 0) {
+    int v = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_syev3_f32<kBulkIn, kComp>, kTPB, 0);
+    cached = (e == cudaSuccess && v > 0) ? v : 1;
+  }
+  return cached;
+}
+
+template <bool kBulkIn, bool kComp>
+cudaError_t launch(const float* A, int64_t n, float* lam, float* U, unsigned long long* counters,
+                   cudaStream_t stream, int sms) {
+  const int64_t n_tiles = (n + kTPB - 1) / kTPB;
+  const int64_t resident = (int64_t)sms * blocks_per_sm_f32<kBulkIn, kComp>();
+  const int grid = (int)(n_tiles < resident ? n_tiles : resident);
+  k_syev3_f32<kBulkIn, kComp><<<grid, kTPB, 0, stream>>>(A, n, lam, U, counters);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_f32(const float* A, int64_t n, float* lam, float* U, bool compensated,
+                       unsigned long long* counters, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const bool bulk = (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+  if (bulk)
+    return compensated ? launch<true, true>(A, n, lam, U, counters, stream, sms)
+                       : launch<true, false>(A, n, lam, U, counters, stream, sms);
+  return compensated ? launch<false, true>(A, n, lam, U, counters, stream, sms)
+                     : launch<false, false>(A, n, lam, U, counters, stream, sms);
+}
+
+cudaError_t take_flags_f32(unsigned* flags) {
+  unsigned v = 0, zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_flags32, sizeof(v));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(g_flags32, &zero, sizeof(zero));
+  *flags |= v;
+  return e;
+}
+
+}  // namespace syev3

@@ -1,0 +1,193 @@
+"""FP32 parity of the CUDA path (plain and compensated) with the FP64 oracle.
+
+The oracle solves the FP32 inputs exactly as given (upcast to FP64).  Bar:
+|dlambda| <= 64 eps32 ||A||_F per eigenvalue (the precision form's stated
+tolerance), residual ||AU - U Lambda||_F <= 64 eps32 ||A||_F and
+orthogonality ||U^T U - I||_F <= 64 eps32 (evaluated in FP64 on the FP32
+outputs), eigenvectors within 64 eps32 / relative gap up to sign where the
+gap is >= 1e-2.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1806_06698_gb300 import inputs  # noqa: E402
+
+MODES = ["plain", "compensated"]
+
+
+@pytest.fixture(scope="module")
+def syev3():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_06698_gb300 import build, syev3 as mod
+
+    build.build()
+    return mod
+
+
+def run32(mod, A32, mode, counters=None, vectors=True):
+    A = torch.from_numpy(np.ascontiguousarray(A32, dtype=np.float32)).cuda()
+    lam, U = mod.syev3_batched(A, vectors=vectors, compensated=(mode == "compensated"), counters=counters)
+    torch.cuda.synchronize()
+    return lam.cpu().numpy(), (U.cpu().numpy() if U is not None else None)
+
+
+def vec_gap_filtered_compare(A32, lam, U, lam_o, U_o):
+    """The FP32 bar: eigenvalues, residual and orthogonality everywhere;
+    eigenvectors up to sign where the relative gap is >= 1e-2."""
+    A64 = np.asarray(A32, np.float64)
+    parity.compare(A64, lam, None, lam_o, None, eps=parity.EPS32, lam_tol=64, res_tol=0, orth_tol=0, vec_tol=0)
+    nrm = parity.fro(A64)
+    ok = nrm > 0
+    res = parity.residual(A64, lam, U) / np.where(ok, nrm, 1.0)
+    assert np.all(res <= 64 * parity.EPS32), f"residual {res.max() / parity.EPS32:.1f} eps32 ||A||_F"
+    orth = parity.orthogonality(U)
+    assert np.all(orth <= 64 * parity.EPS32), f"orthogonality {orth.max() / parity.EPS32:.1f} eps32"
+    assert np.all(parity.sign_rule_holds(U)), "sign rule violated"
+    gap = np.min(np.diff(lam_o, axis=1), axis=1) / np.where(ok, nrm, 1.0)
+    sel = ok & (gap >= 1e-2)
+    for k in range(3):
+        d = np.minimum(np.linalg.norm(U[sel, :, k] - U_o[sel, :, k], axis=1),
+                       np.linalg.norm(U[sel, :, k] + U_o[sel, :, k], axis=1))
+        assert np.all(d <= 64 * parity.EPS32 / gap[sel]), (k, float(np.max(d * gap[sel] / parity.EPS32)))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_gaussian_4096(syev3, mode):
+    A = inputs.gaussian(4096).astype(np.float32)
+    lam, U = run32(syev3, A, mode)
+    lam_o, U_o = oracle.syev3(A.astype(np.float64))
+    vec_gap_filtered_compare(A, lam, U, lam_o, U_o)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n", [1, 3, 127, 128, 129, 255, 3 * 128 + 37, 20011])
+def test_mixed_fp32_ragged(syev3, mode, n):
+    A, _ = inputs.mixed_fp32(n, seed=2000 + n)
+    lam, U = run32(syev3, A, mode)
+    lam_o, U_o = oracle.syev3(A.astype(np.float64))
+    vec_gap_filtered_compare(A, lam, U, lam_o, U_o)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_fp32_subsets(syev3, mode):
+    A, ids = inputs.mixed_fp32(1 << 16, seed=2077)
+    ctr = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device="cuda")
+    lam, U = run32(syev3, A, mode, counters=ctr)
+    lam_o, U_o = oracle.syev3(A.astype(np.float64))
+    for s in inputs.SUBSET_NAMES:
+        m = ids == s
+        vec_gap_filtered_compare(A[m], lam[m], U[m], lam_o[m], U_o[m])
+    c = ctr.cpu().numpy()
+    assert c[0] == 0 and c[1] == 0 and c[3] == 0
+    if mode == "compensated":
+        assert c[2] > 0  # the clustered subset is flagged for FP64 refinement
+    else:
+        assert c[2] == 0
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_structure_tensors(syev3, mode):
+    A = inputs.structure_tensors(50000).astype(np.float32)
+    lam, U = run32(syev3, A, mode)
+    lam_o, U_o = oracle.syev3(A.astype(np.float64))
+    vec_gap_filtered_compare(A, lam, U, lam_o, U_o)
+    assert np.all(lam_o[:, 0] >= -64 * parity.EPS32 * parity.fro(A))  # PSD
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_special_inputs(syev3, mode):
+    A = inputs.gaussian(300, seed=81).astype(np.float32)
+    A[0] = 0.0
+    A[1, 2] = np.nan
+    A[2, 4] = np.inf
+    A[3] = [3.0, -1.0, 3.0, 0.0, 0.0, 0.0]
+    ctr = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device="cuda")
+    lam, U = run32(syev3, A, mode, counters=ctr)
+    assert ctr[1].item() == 2
+    assert np.array_equal(lam[0], np.zeros(3)) and np.array_equal(U[0], np.eye(3))
+    assert np.all(np.isnan(lam[1:3])) and np.all(np.isnan(U[1:3]))
+    assert np.array_equal(lam[3], np.array([-1.0, 3.0, 3.0], np.float32))
+    lam_o, U_o = oracle.syev3(A[3:].astype(np.float64))
+    vec_gap_filtered_compare(A[3:], lam[3:], U[3:], lam_o, U_o)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_unaligned_and_eigenvalues_only(syev3, mode):
+    A, _ = inputs.mixed_fp32(999, seed=2099)
+    buf = torch.zeros(999 * 6 + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = torch.from_numpy(A.reshape(-1)).cuda()
+    lam_b = torch.zeros(999 * 3 + 1, dtype=torch.float32, device="cuda")
+    U_b = torch.zeros(999 * 9 + 1, dtype=torch.float32, device="cuda")
+    lam_v, U_v = lam_b[1:].view(999, 3), U_b[1:].view(999, 3, 3)
+    syev3.syev3_batched(buf[1:].view(999, 6), out=(lam_v, U_v), compensated=(mode == "compensated"))
+    torch.cuda.synchronize()
+    lam_o, U_o = oracle.syev3(A.astype(np.float64))
+    vec_gap_filtered_compare(A, lam_v.cpu().numpy(), U_v.cpu().numpy(), lam_o, U_o)
+    lam_n, U_n = run32(syev3, A, mode, vectors=False)
+    assert U_n is None
+    assert np.array_equal(lam_n, lam_v.cpu().numpy())
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_full_size_fp32_sampled(syev3, mode):
+    """The 2^24 mixed FP32 batch and 2^26 structure tensors in the
+    benchmark's launch: every output checked on the GPU for ordering and
+    orthogonality, 2^14 sampled matrices against the oracle."""
+    for A in (inputs.mixed_fp32(1 << 24)[0], inputs.structure_tensors(1 << 26).astype(np.float32)):
+        n = A.shape[0]
+        At = torch.from_numpy(A).cuda()
+        ctr = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device="cuda")
+        lam, U = syev3.syev3_batched(At, compensated=(mode == "compensated"), counters=ctr)
+        torch.cuda.synchronize()
+        c = ctr.cpu().numpy()
+        assert c[0] == 0 and c[1] == 0 and c[3] == 0
+        assert bool(torch.all(lam[:, 1:] >= lam[:, :-1]))
+        orth = torch.linalg.matrix_norm(U.double().transpose(1, 2) @ U.double()
+                                        - torch.eye(3, dtype=torch.float64, device=U.device))
+        assert float(orth.max()) <= 64 * parity.EPS32
+        rng = np.random.default_rng(7)
+        idx = np.sort(rng.choice(n, 1 << 14, replace=False))
+        it = torch.from_numpy(idx).cuda()
+        lam_s, U_s = lam[it].cpu().numpy(), U[it].cpu().numpy()
+        lam_o, U_o = oracle.syev3(A[idx].astype(np.float64))
+        vec_gap_filtered_compare(A[idx], lam_s, U_s, lam_o, U_o)
+        del At, lam, U
+        torch.cuda.empty_cache()
+
+
+def test_precision_report(syev3, capsys):
+    """Per-subset error of the FP32 forms (and of the FP64 solver on the same
+    upcast inputs) against the FP64 oracle, in units of eps32 ||A||_F."""
+    A_mixed, ids = inputs.mixed_fp32(1 << 17, seed=2100)
+    A_st = inputs.structure_tensors(1 << 16, seed=2101).astype(np.float32)
+    groups = [(inputs.SUBSET_NAMES[s], A_mixed[ids == s]) for s in inputs.SUBSET_NAMES]
+    groups.append(("structure_tensors", A_st))
+    lines = ["subset | form | max |dlam|/(eps32 ||A||) | max residual/(eps32 ||A||) | max ||U^T U - I||/eps32"]
+    for name, A in groups:
+        A64 = A.astype(np.float64)
+        lam_o, U_o = oracle.syev3(A64)
+        nrm = parity.fro(A64)
+        nz = np.where(nrm > 0, nrm, 1.0)
+        for form in ("plain", "compensated", "fp64"):
+            if form == "fp64":
+                At = torch.from_numpy(A64).cuda()
+                lam_t, U_t = syev3.syev3_batched(At)
+                torch.cuda.synchronize()
+                lam, U = lam_t.cpu().numpy(), U_t.cpu().numpy()
+            else:
+                lam, U = run32(syev3, A, form)
+            dl = np.max(np.abs(lam.astype(np.float64) - lam_o), axis=1) / nz / parity.EPS32
+            res = parity.residual(A64, lam, U) / nz / parity.EPS32
+            orth = parity.orthogonality(U) / parity.EPS32
+            lines.append(f"{name} | {form} | {dl.max():.3f} | {res.max():.3f} | {orth.max():.3f}")
+            assert dl.max() <= 64 and res.max() <= 64 and orth.max() <= 64
+    with capsys.disabled():
+        print("\n" + "\n".join(lines))
