@@ -81,18 +81,40 @@ __device__ __forceinline__ Rot ordered_rotation(double p, double q, double r) {
 // b2/(x + ab) > c/2, so the choice is never the less accurate one.
 // f'(x) = 1 + b1/x^2 + b2/(x + ab)^2 (Eq. (3)) and omega_0 are unchanged.
 
-// FP32 Borges-Gragg pass for two problems at once (mu and nu), started from
-// the zero of the limit model Eq. (7).  Each returned start lies right of
+// Start of the Borges-Gragg iteration (FP32).  Sec. 1.4.1 starts from the
+// zero x7 of the limit model Eq. (7), right of the root.  For a root far
+// below abar (clustered spectra, small spikes) x7 can be many orders of
+// magnitude too large, and the iteration then needs 5-10 steps to come down.
+// Near 0, f(x) = (1 + c/ab) x + K - b1/x - c x^2/(ab (x+ab)) + ..., so the
+// zero xm of (1 + c/ab) x^2 + K x - b1 lies just left of the root, by about
+// c xm^2 / (ab^2 f'(xm)); twice that (plus 2^-20 xm) moves it right.  That
+// start is used when it lies below x7 and xm < ab/16; the caller restarts
+// from x7 if f is not positive there.  Returns the start, sets x7.
+__device__ __forceinline__ float start32(const float ab, const float b1, const float b2, const float g,
+                                        const float c, const float K, float& x7, bool& from_model) {
+  const float hg = 0.5f * g, bs = b1 + b2;
+  const float rt = sqrt32(fmaf(hg, hg, bs));
+  x7 = (g >= 0.f) ? hg + rt : bs * rcp32(rt - hg);
+  const float c2 = fmaf(c, rcp32(ab), 1.f);
+  const float disc = sqrt32(fmaf(K, K, 4.f * c2 * b1));
+  const float xm = (K >= 0.f) ? 2.f * b1 * rcp32(K + disc) : (disc - K) * rcp32(2.f * c2);
+  const float r1 = rcp32(xm), r2 = rcp32(xm + ab);
+  const float fpm = fmaf(b2 * r2, r2, fmaf(b1 * r1, r1, 1.f));
+  const float x0 = xm + fmaf(2.f * c * xm * xm, rcp32(ab * ab * fpm), 0x1p-20f * xm);
+  from_model = (xm > 0.f) && (xm < 0.0625f * ab) && (x0 < x7);
+  return from_model ? x0 : x7;
+}
+
+// FP32 Borges-Gragg pass for two problems at once (mu and nu), started by
+// start32 (the zero of the limit model Eq. (7), or the small-root model).  Each returned start lies right of
 // its root by a bound on the FP32 error (checked again in FP64).
 __device__ __forceinline__ void seed32x2(const float ab, const float b1[2], const float b2[2], const float g[2],
                                          const float c[2], const float K[2], float out[2]) {
-  float x[2];
-  bool live[2];
+  float x[2], x7[2];
+  bool live[2], model[2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const float hg = 0.5f * g[k], bs = b1[k] + b2[k];
-    const float rt = sqrt32(fmaf(hg, hg, bs));
-    x[k] = (g[k] >= 0.f) ? hg + rt : bs * rcp32(rt - hg);
+    x[k] = start32(ab, b1[k], b2[k], g[k], c[k], K[k], x7[k], model[k]);
     live[k] = true;
     out[k] = 0.f;
   }
@@ -108,6 +130,13 @@ __device__ __forceinline__ void seed32x2(const float ab, const float b1[2], cons
       const float u = small ? c[k] * x[k] * r2 : -t2;
       const float f = ((x[k] + lead) - t1) + u;
       const float fp = fmaf(t2, r2, fmaf(t1, r1, 1.f));
+      if (model[k]) {  // first evaluation at the small-root start: keep it only if right of the root
+        model[k] = false;
+        if (!(f > 0.f)) {
+          x[k] = x7[k];
+          continue;
+        }
+      }
       bool done = !(f > (4.f * kEps32) * x[k] * fp) || it == kSeedIt;
       float xn = x[k];
       if (!done) {

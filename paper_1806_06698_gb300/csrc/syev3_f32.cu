@@ -158,17 +158,17 @@ __device__ __forceinline__ Lane32 make_lane32(const float a_in[6]) {
   return L;
 }
 
-// Borges-Gragg in FP32 for mu and nu together (Sec. 1.4.1), started from the
-// zero of Eq. (7); stops when f/f' < C eps32 x, when f <= 0 or when a step no
-// longer moves x.  For x < ab, f = x + K - b1/x + c x/(x+ab).
+// Borges-Gragg in FP32 for mu and nu together (Sec. 1.4.1), started by
+// f64::start32 (Eq. (7), or the small-root model); stops when
+// f/f' < C eps32 x, when f <= 0 or when a step no longer moves x.  For
+// x < ab, f = x + K - b1/x + c x/(x+ab).
 __device__ __forceinline__ void roots32(const float ab, const float b1[2], const float b2[2], const float g[2],
                                         const float c[2], const float K[2], float x[2], bool& capped) {
-  bool live[2];
+  bool live[2], model[2];
+  float x7[2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const float hg = 0.5f * g[k], bs = b1[k] + b2[k];
-    const float rt = sqrt32(fmaf(hg, hg, bs));
-    x[k] = (g[k] >= 0.f) ? hg + rt : bs * rcp32(rt - hg);
+    x[k] = f64::start32(ab, b1[k], b2[k], g[k], c[k], K[k], x7[k], model[k]);
     live[k] = true;
   }
   capped = false;
@@ -182,6 +182,13 @@ __device__ __forceinline__ void roots32(const float ab, const float b1[2], const
       const bool small = x[k] < ab;
       const float f = ((x[k] + (small ? K[k] : -g[k])) - t1) + (small ? c[k] * x[k] * r2 : -t2);
       const float fp = fmaf(t2, r2, fmaf(t1, r1, 1.f));
+      if (model[k]) {  // first evaluation at the small-root start: keep it only if right of the root
+        model[k] = false;
+        if (!(f > 0.f)) {
+          x[k] = x7[k];
+          continue;
+        }
+      }
       if (!(f > 0.f) || f < (kCTerm32 * kEps32) * x[k] * fp) {
         live[k] = false;
         continue;
