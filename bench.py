@@ -248,6 +248,53 @@ def _fp32_legs(args, dev, stream, barrier, A64_dev):
     return out
 
 
+BWD_BYTES = {"f64": 240, "f32": 120}  # lambda, U, g_lambda, g_U in + packed gradient out
+# Algorithmic operations of one backward: the antisymmetric part of U^T gU
+# (36), ||A||_F and the gaps (9), the masked couplings (12), P = U sym(C)
+# (45), the upper triangle of P U^T (33) and the doubling (3).
+BWD_FLOPS = 138
+
+
+def _bwd_legs(args, dev, stream, barrier):
+    """Differentiation form: 2^20 matrices Q diag(d) Q^T (95 % gaps >= 1e-3,
+    5 % near-degenerate, masked with tau = 1e-6), loss sum w lambda + sum V o U,
+    the backward kernel timed alone in FP64 and FP32."""
+    import torch
+
+    from paper_1806_06698_gb300 import inputs, syev3
+
+    n = max(1, args.n // 16)
+    A_np, _, _ = inputs.spectral(n, seed=inputs.SEED_BASE + 4)
+    rng = np.random.default_rng(inputs.SEED_BASE + 6)
+    wn, Vn = rng.standard_normal((n, 3)), rng.standard_normal((n, 3, 3))
+    hbm = load_peaks().get("hbm_gbs", 6686.1)
+    out = {}
+    for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+        A = torch.from_numpy(A_np).to(dev, dt)
+        lam, U = syev3.syev3_batched(A, stream=stream)
+        w, V = torch.from_numpy(wn).to(dev, dt), torch.from_numpy(Vn).to(dev, dt)
+        gA = torch.empty((n, 6), dtype=dt, device=dev)
+
+        def step():
+            syev3.syev3_batched_bwd(lam, U, w, V, 1e-6, out=gA, stream=stream)
+
+        total_ms, kms = _timed(step, args.steps, args.warmup, stream, barrier)
+        k = statistics.mean(kms)
+        rate = n / (k * 1e-3)
+        if name == "f64":
+            roof = {"bound": "alu", "achieved": BWD_FLOPS * rate / 1e12, "peak": FP64_PEAK_GFLOPS / 1e3,
+                    "unit": "TFLOP/s", "frac": BWD_FLOPS * rate / 1e9 / FP64_PEAK_GFLOPS,
+                    "hbm_frac_of_measured": BWD_BYTES[name] * rate / 1e9 / hbm}
+        else:
+            roof = {"bound": "hbm", "achieved": BWD_BYTES[name] * rate / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac": BWD_BYTES[name] * rate / 1e9 / hbm}
+        roof.update({"kernel": "k_syev3_bwd", "traffic": None})
+        out[f"backward_{name}_2^20"] = {"value": n * args.steps / (total_ms * 1e-3), "unit": "gradients/s",
+                                        "ms_per_step": total_ms / args.steps, "n": n, "roofline": roof}
+        del A, lam, U, w, V, gA
+    return out
+
+
 def run_native(args):
     import torch
 
@@ -309,6 +356,7 @@ def run_native(args):
     e2e_value = ws * n * e2e_steps / (e2e_ms * 1e-3)
 
     fp32 = None if args.fp64_only else _fp32_legs(args, dev, stream, barrier, A)
+    bwd = None if args.fp64_only else _bwd_legs(args, dev, stream, barrier)
 
     if rank == 0:
         kms = statistics.mean(kernel_ms)
@@ -336,6 +384,8 @@ def run_native(args):
         }
         if fp32 is not None:
             line["precision_form"] = fp32
+        if bwd is not None:
+            line["differentiation_form"] = bwd
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(A_np, n)
         print(json.dumps(line), flush=True)

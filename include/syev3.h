@@ -94,6 +94,27 @@ int syev3_batched(const void* A_packed6, int64_t n, void* lambda, void* U, int d
 int syev3_batched_ex(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype,
                      uint64_t* d_counters, syev3_stream_t stream);
 
+/* syev3_batched_bwd -- gradient of a loss through syev3_batched, packed.
+ * Not in the paper: the standard derivative of simple eigenpairs,
+ *   Abar = U (diag(g_lambda) + F o (U^T g_U)) U^T,
+ *   F_ij = 1/(lambda_j - lambda_i) for i != j, and F_ij = 0 where
+ *   |lambda_i - lambda_j| < gap_tau * ||A||_F (||A||_F = ||lambda||_2);
+ * g_A_packed6 receives (Abar_11, Abar_22, Abar_33, Abar_12 + Abar_21,
+ * Abar_13 + Abar_31, Abar_23 + Abar_32): the gradient with respect to the
+ * packed entries (a11, a22, a33, a12, a13, a23).
+ *   lambda, U   : device, the outputs of syev3_batched (n x 3, n x 9).
+ *   g_lambda    : device, n x 3, gradient of the loss with respect to lambda.
+ *   g_U         : device, n x 9, gradient with respect to U, or NULL (zero).
+ *   n           : >= 0.
+ *   g_A_packed6 : device, n x 6, written; must not overlap the inputs.
+ *   gap_tau     : >= 0; eigenvector coupling of closer pairs is dropped.
+ *   dtype       : SYEV3_F64, or SYEV3_F32 / SYEV3_F32_COMPENSATED (FP32).
+ * Returns SYEV3_EINVAL (NULL required buffer, n < 0, negative or
+ * non-finite gap_tau, misaligned, overlapping or host-pageable buffers) or
+ * SYEV3_ECUDA; SYEV3_OK otherwise.  Asynchronous on `stream`. */
+int syev3_batched_bwd(const void* lambda, const void* U, const void* g_lambda, const void* g_U, int64_t n,
+                      void* g_A_packed6, double gap_tau, int dtype, syev3_stream_t stream);
+
 /* Device-side status bits of the current device, OR-ed over all launches
  * since the last call, then cleared (synchronises the device).
  *   bit 0: a bulk-copy wait timed out (SYEV3_ETIMEOUT). */

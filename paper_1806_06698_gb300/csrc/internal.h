@@ -16,9 +16,14 @@ cudaError_t launch_f64(const double* A, int64_t n, double* lam, double* U, unsig
 cudaError_t launch_f32(const float* A, int64_t n, float* lam, float* U, bool compensated,
                        unsigned long long* counters, cudaStream_t stream);
 
+template <class T>
+cudaError_t launch_bwd(const T* lam, const T* U, const T* gl, const T* gU, int64_t n, T* gA, T tau,
+                       cudaStream_t stream);
+
 // Read and clear the __device__ status word of each translation unit
 // (synchronise the device).
 cudaError_t take_flags_f64(unsigned* flags);
 cudaError_t take_flags_f32(unsigned* flags);
+cudaError_t take_flags_bwd(unsigned* flags);
 
 }  // namespace syev3

@@ -103,6 +103,34 @@ int syev3_batched(const void* A_packed6, int64_t n, void* lambda, void* U, int d
   return syev3_batched_ex(A_packed6, n, lambda, U, dtype, nullptr, stream);
 }
 
+int syev3_batched_bwd(const void* lambda, const void* U, const void* g_lambda, const void* g_U, int64_t n,
+                      void* g_A_packed6, double gap_tau, int dtype, syev3_stream_t stream) {
+  if (!valid_dtype(dtype) || n < 0 || !(gap_tau >= 0.0) || gap_tau > 1e300) return SYEV3_EINVAL;
+  if (n == 0) return SYEV3_OK;
+  if (lambda == nullptr || U == nullptr || g_lambda == nullptr || g_A_packed6 == nullptr) return SYEV3_EINVAL;
+  const size_t es = elem_size(dtype);
+  const void* ins[4] = {lambda, U, g_lambda, g_U};
+  const size_t nbs[4] = {(size_t)n * 3 * es, (size_t)n * 9 * es, (size_t)n * 3 * es, (size_t)n * 9 * es};
+  const size_t nb_out = (size_t)n * 6 * es;
+  for (int i = 0; i < 4; ++i) {
+    if (ins[i] == nullptr) continue;
+    if (!aligned(ins[i], es) || overlap(ins[i], nbs[i], g_A_packed6, nb_out) || !device_accessible(ins[i]))
+      return SYEV3_EINVAL;
+  }
+  if (!aligned(g_A_packed6, es) || !device_accessible(g_A_packed6)) return SYEV3_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (dtype == SYEV3_F64)
+    e = syev3::launch_bwd<double>(static_cast<const double*>(lambda), static_cast<const double*>(U),
+                                  static_cast<const double*>(g_lambda), static_cast<const double*>(g_U), n,
+                                  static_cast<double*>(g_A_packed6), gap_tau, s);
+  else
+    e = syev3::launch_bwd<float>(static_cast<const float*>(lambda), static_cast<const float*>(U),
+                                 static_cast<const float*>(g_lambda), static_cast<const float*>(g_U), n,
+                                 static_cast<float*>(g_A_packed6), (float)gap_tau, s);
+  return e == cudaSuccess ? SYEV3_OK : cuda_fail(e);
+}
+
 int syev3_device_flags(uint32_t* flags) {
   if (flags == nullptr) return SYEV3_EINVAL;
   cudaError_t e = cudaDeviceSynchronize();
@@ -110,6 +138,7 @@ int syev3_device_flags(uint32_t* flags) {
   unsigned v = 0;
   e = syev3::take_flags_f64(&v);
   if (e == cudaSuccess) e = syev3::take_flags_f32(&v);
+  if (e == cudaSuccess) e = syev3::take_flags_bwd(&v);
   if (e != cudaSuccess) return cuda_fail(e);
   *flags = v;
   return SYEV3_OK;

@@ -52,6 +52,8 @@ def _load():
             lib.syev3_batched.restype = i32
             lib.syev3_batched_ex.argtypes = [vp, i64, vp, vp, i32, vp, vp]
             lib.syev3_batched_ex.restype = i32
+            lib.syev3_batched_bwd.argtypes = [vp, vp, vp, vp, i64, vp, ctypes.c_double, i32, vp]
+            lib.syev3_batched_bwd.restype = i32
             lib.syev3_device_flags.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
             lib.syev3_device_flags.restype = i32
             _lib = lib
@@ -120,3 +122,46 @@ def device_flags() -> int:
     v = ctypes.c_uint32(0)
     _check(lib.syev3_device_flags(ctypes.byref(v)), "syev3_device_flags")
     return int(v.value)
+
+
+def syev3_batched_bwd(lam: torch.Tensor, U: torch.Tensor, g_lam: torch.Tensor, g_U: torch.Tensor | None,
+                      gap_tau: float = 1e-6, *, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Packed (n, 6) gradient of a loss through (lam, U) of syev3_batched:
+    Abar = U (diag(g_lam) + F o (U^T g_U)) U^T with F_ij = 1/(lam_j - lam_i),
+    pairs closer than gap_tau * ||A||_F masked; off-diagonal packed entries
+    hold Abar_ij + Abar_ji."""
+    for t in (lam, U, g_lam) + ((g_U,) if g_U is not None else ()):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("backward inputs must be contiguous CUDA tensors (no CPU fallback)")
+    n = lam.shape[0]
+    code = SYEV3_F64 if lam.dtype == torch.float64 else SYEV3_F32
+    gA = torch.empty((n, 6), dtype=lam.dtype, device=lam.device) if out is None else out
+    lib = _load()
+    st = lib.syev3_batched_bwd(_ptr(lam), _ptr(U), _ptr(g_lam), _ptr(g_U), n, _ptr(gA), float(gap_tau), code,
+                               _stream(stream))
+    _check(st, "syev3_batched_bwd")
+    return gA
+
+
+class Syev3Function(torch.autograd.Function):
+    """(lam, U) = eigh of packed symmetric 3x3 matrices, differentiable:
+    the backward pass is the library's k_syev3_bwd kernel."""
+
+    @staticmethod
+    def forward(ctx, A6, compensated: bool = False, gap_tau: float = 1e-6):
+        lam, U = syev3_batched(A6, compensated=compensated)
+        ctx.save_for_backward(lam, U)
+        ctx.gap_tau = gap_tau
+        return lam, U
+
+    @staticmethod
+    def backward(ctx, g_lam, g_U):
+        lam, U = ctx.saved_tensors
+        g_lam = torch.zeros_like(lam) if g_lam is None else g_lam.contiguous()
+        g_U = None if g_U is None else g_U.contiguous()
+        return syev3_batched_bwd(lam, U, g_lam, g_U, ctx.gap_tau), None, None
+
+
+def eigh3(A6: torch.Tensor, compensated: bool = False, gap_tau: float = 1e-6):
+    """Differentiable batched eigendecomposition of packed (n, 6) matrices."""
+    return Syev3Function.apply(A6, compensated, gap_tau)
