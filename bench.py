@@ -51,7 +51,9 @@ def parse():
     p.add_argument("--impl", choices=["native", "reference"], default="native")
     p.add_argument("--n", type=int, default=N_MATRICES, help=argparse.SUPPRESS)
     p.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
-    p.add_argument("--fp64-only", action="store_true", help="skip the FP32 precision-form legs")
+    p.add_argument("--fp64-only", action="store_true", help="only the FP64 headline leg")
+    p.add_argument("--serve-seconds", type=float, default=10.0,
+                   help="length of the Poisson serving run (the full configuration is 60)")
     return p.parse_args()
 
 
@@ -295,6 +297,72 @@ def _bwd_legs(args, dev, stream, barrier):
     return out
 
 
+def _serving_leg(args, dev, A64):
+    """Serving form: Poisson arrivals at 2000 requests/s for --serve-seconds,
+    each request N = floor(exp(U(0, ln 2^22))) matrices, 70 % FP64 / 30 %
+    FP32 (compensated), sliced from device-resident pools of the mixed
+    batches, through a server with a 16 GiB budget.  Latency = the library's
+    own submit -> done timestamps."""
+    import threading
+
+    import torch
+
+    from paper_1806_06698_gb300 import inputs, syev3
+
+    A32 = torch.from_numpy(inputs.mixed_fp32(A64.shape[0])[0]).to(dev)
+    rng = np.random.default_rng(inputs.SEED_BASE + 7)
+    rate, T = 2000.0, float(args.serve_seconds)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, int(rate * T * 1.2) + 16))
+    arrivals = arrivals[arrivals < T]
+    m = len(arrivals)
+    sizes = np.floor(np.exp(rng.uniform(0.0, np.log(2.0 ** 22), m))).astype(np.int64)
+    sizes = np.minimum(sizes, A64.shape[0])
+    is64 = rng.uniform(0, 1, m) < 0.7
+    offs = (rng.uniform(0, 1, m) * (A64.shape[0] - sizes + 1)).astype(np.int64)
+    srv = syev3.Server(memory_budget_bytes=16 << 30, num_streams=4, chunk=1 << 18, max_inflight=2)
+    for k in range(8):  # warm-up requests
+        srv.wait(srv.submit(A64[: 1 << 16]), 60.0)
+    tickets = [None] * m
+    ready = threading.Semaphore(0)
+
+    def client():
+        t0 = time.perf_counter()
+        for i in range(m):
+            dt = arrivals[i] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            pool = A64 if is64[i] else A32
+            tickets[i] = srv.submit(pool[offs[i]:offs[i] + sizes[i]], compensated=not is64[i])
+            ready.release()
+
+    lat, t_first, t_last, waited = [], None, 0, 0
+    th = threading.Thread(target=client)
+    th.start()
+    for i in range(m):
+        ready.acquire()
+        info = srv.wait(tickets[i], 120.0)
+        lat.append((info.t_done_ns - info.t_submit_ns) * 1e-6)
+        t_first = info.t_submit_ns if t_first is None else min(t_first, info.t_submit_ns)
+        t_last = max(t_last, info.t_done_ns)
+        waited += info.t_admit_ns - info.t_submit_ns > 1_000_000
+        srv.release(tickets[i])
+    th.join()
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    total = int(sizes.sum())
+    span = (t_last - t_first) * 1e-9
+    return {"requests": m, "seconds": T, "arrival_rate_per_s": rate, "matrices": total,
+            "offered_matrices_per_s": total / T, "value": total / span, "unit": UNIT,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "mean_ms": float(lat.mean()),
+            "p99_ms_small_requests_le_4096": float(np.percentile(lat[sizes <= 4096], 99)),
+            "arena_peak_bytes": int(st.arena_peak), "memory_budget_bytes": 16 << 30,
+            "waited_for_memory_over_1ms": int(waited), "chunks": int(st.chunks),
+            "config": "Poisson 2000 req/s, N log-uniform [1, 2^22], 70% FP64 / 30% FP32 compensated, "
+                      "4 streams, chunks of 2^18, 16 GiB budget"}
+
+
 def run_native(args):
     import torch
 
@@ -357,6 +425,7 @@ def run_native(args):
 
     fp32 = None if args.fp64_only else _fp32_legs(args, dev, stream, barrier, A)
     bwd = None if args.fp64_only else _bwd_legs(args, dev, stream, barrier)
+    serving = None if (args.fp64_only or args.serve_seconds <= 0) else _serving_leg(args, dev, A)
 
     if rank == 0:
         kms = statistics.mean(kernel_ms)
@@ -386,6 +455,8 @@ def run_native(args):
             line["precision_form"] = fp32
         if bwd is not None:
             line["differentiation_form"] = bwd
+        if serving is not None:
+            line["serving"] = serving
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(A_np, n)
         print(json.dumps(line), flush=True)

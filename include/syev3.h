@@ -120,6 +120,68 @@ int syev3_batched_bwd(const void* lambda, const void* U, const void* g_lambda, c
  *   bit 0: a bulk-copy wait timed out (SYEV3_ETIMEOUT). */
 int syev3_device_flags(uint32_t* flags);
 
+/* ------------------------------------------------------------------------
+ * Serving: a continuous-batching request server (not in the paper).
+ *
+ * Requests reference packed matrices already in device memory and receive
+ * their eigenvalues (and eigenvectors) in a device arena of fixed size -- the
+ * memory budget -- allocated once by syev3_server_create.  A dispatcher
+ * thread admits waiting requests in arrival order as the arena frees up,
+ * cuts them into chunks and issues the chunks round-robin across all
+ * admitted requests onto `num_streams` CUDA streams (at most `max_inflight`
+ * per stream), so requests arriving while others run share the device.
+ * Results stay in the arena until syev3_server_release.
+ * ------------------------------------------------------------------------ */
+typedef struct syev3_server_s syev3_server;
+
+typedef struct {
+  size_t memory_budget_bytes; /* device arena for results; 0 = 16 GiB */
+  int num_streams;            /* 0 = 4 */
+  int64_t chunk;              /* matrices per launch; 0 = 2^18 */
+  int max_inflight;           /* chunks in flight per stream; 0 = 2 */
+} syev3_server_config;
+
+typedef struct {
+  int state;        /* 0 waiting for memory, 1 admitted, 2 done, 3 failed */
+  int dtype;
+  int64_t n;
+  void* d_lambda;   /* device, n x 3 (valid once admitted; final when done) */
+  void* d_U;        /* device, n x 9, or NULL when vectors were not asked for */
+  int64_t t_submit_ns, t_admit_ns, t_done_ns; /* host steady clock */
+} syev3_request_info;
+
+typedef struct {
+  int64_t completed, matrices, chunks, waiting;
+  size_t arena_bytes, arena_used, arena_peak;
+  int error;        /* first failure status, or SYEV3_OK */
+} syev3_server_stats;
+
+/* Creates a server on the current device; cfg may be NULL (defaults).
+ * Allocates the arena with cudaMalloc: SYEV3_ECUDA if that fails. */
+int syev3_server_create(const syev3_server_config* cfg, syev3_server** out);
+
+/* Stops the dispatcher, waits for work in flight, frees the arena. */
+int syev3_server_destroy(syev3_server* srv);
+
+/* Queues a request: n >= 1 packed matrices at d_A (device, dtype as in
+ * syev3_batched, must stay valid until the request is done).  Returns at
+ * once with a ticket; SYEV3_EINVAL if the outputs could never fit the
+ * arena. */
+int syev3_server_submit(syev3_server* srv, int dtype, const void* d_A, int64_t n, int vectors,
+                        uint64_t* ticket);
+
+/* State, result pointers and timestamps of a request (non-blocking). */
+int syev3_server_query(syev3_server* srv, uint64_t ticket, syev3_request_info* info);
+
+/* Blocks until the request is done (SYEV3_OK), failed (its error) or
+ * timeout_s passed (SYEV3_ETIMEOUT). */
+int syev3_server_wait(syev3_server* srv, uint64_t ticket, double timeout_s);
+
+/* Frees a done request's results (SYEV3_EINVAL if not done). */
+int syev3_server_release(syev3_server* srv, uint64_t ticket);
+
+int syev3_server_get_stats(syev3_server* srv, syev3_server_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

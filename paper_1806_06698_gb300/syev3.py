@@ -165,3 +165,113 @@ class Syev3Function(torch.autograd.Function):
 def eigh3(A6: torch.Tensor, compensated: bool = False, gap_tau: float = 1e-6):
     """Differentiable batched eigendecomposition of packed (n, 6) matrices."""
     return Syev3Function.apply(A6, compensated, gap_tau)
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("memory_budget_bytes", ctypes.c_size_t), ("num_streams", ctypes.c_int),
+                ("chunk", ctypes.c_int64), ("max_inflight", ctypes.c_int)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("dtype", ctypes.c_int), ("n", ctypes.c_int64),
+                ("d_lambda", ctypes.c_void_p), ("d_U", ctypes.c_void_p), ("t_submit_ns", ctypes.c_int64),
+                ("t_admit_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("matrices", ctypes.c_int64), ("chunks", ctypes.c_int64),
+                ("waiting", ctypes.c_int64), ("arena_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t),
+                ("arena_peak", ctypes.c_size_t), ("error", ctypes.c_int)]
+
+
+def _bind_server(lib):
+    if getattr(lib, "_server_bound", False):
+        return
+    vp = ctypes.c_void_p
+    lib.syev3_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)]
+    lib.syev3_server_destroy.argtypes = [vp]
+    lib.syev3_server_submit.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_uint64)]
+    lib.syev3_server_query.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(RequestInfo)]
+    lib.syev3_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double]
+    lib.syev3_server_release.argtypes = [vp, ctypes.c_uint64]
+    lib.syev3_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    for f in ("syev3_server_create", "syev3_server_destroy", "syev3_server_submit", "syev3_server_query",
+              "syev3_server_wait", "syev3_server_release", "syev3_server_get_stats"):
+        getattr(lib, f).restype = ctypes.c_int
+    lib._server_bound = True
+
+
+class Server:
+    """Continuous-batching request server (see include/syev3.h).  Requests
+    are device tensors of packed matrices; results stay in the server's
+    device arena until released."""
+
+    def __init__(self, memory_budget_bytes: int = 16 << 30, num_streams: int = 4, chunk: int = 1 << 18,
+                 max_inflight: int = 2):
+        self._lib = _load()
+        _bind_server(self._lib)
+        cfg = _ServerConfig(memory_budget_bytes, num_streams, chunk, max_inflight)
+        h = ctypes.c_void_p()
+        _check(self._lib.syev3_server_create(ctypes.byref(cfg), ctypes.byref(h)), "syev3_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, A6: torch.Tensor, compensated: bool = False, vectors: bool = True) -> int:
+        if not A6.is_cuda or not A6.is_contiguous() or A6.dim() != 2 or A6.shape[1] != 6:
+            raise ValueError("A6 must be a contiguous (n, 6) CUDA tensor")
+        t = ctypes.c_uint64()
+        st = self._lib.syev3_server_submit(self._h, dtype_code(A6.dtype, compensated), _ptr(A6), A6.shape[0],
+                                           int(vectors), ctypes.byref(t))
+        _check(st, "syev3_server_submit")
+        self._keep[t.value] = A6  # the input must outlive the request
+        return t.value
+
+    def query(self, ticket: int) -> RequestInfo:
+        info = RequestInfo()
+        _check(self._lib.syev3_server_query(self._h, ticket, ctypes.byref(info)), "syev3_server_query")
+        return info
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> RequestInfo:
+        _check(self._lib.syev3_server_wait(self._h, ticket, float(timeout_s)), "syev3_server_wait")
+        return self.query(ticket)
+
+    def results(self, ticket: int):
+        """(lambda, U) of a done request: tensors viewing the server's arena
+        (no copy); clone them before release if they are to be kept."""
+        info = self.query(ticket)
+        dt = self._keep[ticket].dtype
+        lam = _device_view(info.d_lambda, (info.n, 3), dt)
+        U = _device_view(info.d_U, (info.n, 3, 3), dt) if info.d_U else None
+        return lam, U
+
+    def release(self, ticket: int):
+        _check(self._lib.syev3_server_release(self._h, ticket), "syev3_server_release")
+        self._keep.pop(ticket, None)
+
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        _check(self._lib.syev3_server_get_stats(self._h, ctypes.byref(st)), "syev3_server_get_stats")
+        return st
+
+    def close(self):
+        if self._h:
+            self._lib.syev3_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceArray:
+    def __init__(self, ptr: int, shape, dtype):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8" if dtype == torch.float64 else "<f4",
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def _device_view(ptr: int, shape, dtype) -> torch.Tensor:
+    """A tensor viewing library-owned device memory at ``ptr``."""
+    return torch.as_tensor(_DeviceArray(ptr, shape, dtype), device="cuda")

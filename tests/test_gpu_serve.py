@@ -1,0 +1,111 @@
+"""Serving form: the continuous-batching server returns, for every request,
+the same result as a standalone call on the same matrices (bit for bit),
+never exceeds its memory budget, admits requests as memory frees up, and
+lets requests that arrive while a large one runs finish before it."""
+
+import threading
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1806_06698_gb300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def syev3():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_06698_gb300 import build, syev3 as mod
+
+    build.build()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def pools():
+    A64 = torch.from_numpy(inputs.mixed(1 << 20, seed=4000)[0]).cuda()
+    A32 = torch.from_numpy(inputs.mixed_fp32(1 << 20, seed=4001)[0]).cuda()
+    return A64, A32
+
+
+def standalone(syev3, A, comp):
+    lam, U = syev3.syev3_batched(A, compensated=comp)
+    torch.cuda.synchronize()
+    return lam, U
+
+
+def test_same_alone_and_in_the_mix(syev3, pools):
+    """Requests of uneven sizes and mixed dtypes, submitted from a client
+    thread while earlier ones run, through a small budget that makes some
+    wait for memory and small chunks that interleave them."""
+    A64, A32 = pools
+    rng = np.random.default_rng(4002)
+    budget = 48 << 20
+    srv = syev3.Server(memory_budget_bytes=budget, num_streams=4, chunk=1 << 12, max_inflight=2)
+    reqs = []
+    for i in range(160):
+        n = int(np.exp(rng.uniform(0, np.log(1 << 17))))
+        kind = rng.choice(["f64", "f32", "f32c"], p=[0.6, 0.2, 0.2])
+        pool = A64 if kind == "f64" else A32
+        off = int(rng.integers(0, pool.shape[0] - n))
+        reqs.append((pool[off:off + n], kind == "f32c"))
+    tickets = [None] * len(reqs)
+
+    def client():
+        for i, (A, comp) in enumerate(reqs):
+            tickets[i] = srv.submit(A, compensated=comp)
+            if i % 7 == 0:
+                time.sleep(0.0005)
+
+    th = threading.Thread(target=client)
+    th.start()
+    th.join()
+    waited = 0
+    for i, (A, comp) in enumerate(reqs):
+        info = srv.wait(tickets[i], 60.0)
+        assert info.state == 2 and info.n == A.shape[0]
+        waited += info.t_admit_ns > info.t_submit_ns + 200_000
+        lam, U = srv.results(tickets[i])
+        lam_s, U_s = standalone(syev3, A, comp)
+        assert torch.equal(lam, lam_s) and torch.equal(U, U_s), i
+        srv.release(tickets[i])
+    st = srv.stats()
+    assert st.completed == len(reqs) and st.waiting == 0 and st.error == 0
+    assert st.arena_peak <= budget and st.arena_used == 0
+    assert st.chunks > len(reqs)  # large requests were cut into chunks
+    srv.close()
+
+
+def test_small_requests_overtake_a_large_one(syev3, pools):
+    """Continuous batching: requests that arrive while a large request is on
+    the device are admitted and finish before it does."""
+    A64, _ = pools
+    srv = syev3.Server(memory_budget_bytes=1 << 30, num_streams=4, chunk=1 << 14, max_inflight=1)
+    big = srv.submit(A64)  # 2^20 matrices, 64 chunks
+    while srv.query(big).state == 0:
+        time.sleep(0.0001)
+    small = [srv.submit(A64[i * 97:(i * 97) + 64]) for i in range(16)]
+    done_small = [srv.wait(t, 60.0).t_done_ns for t in small]
+    done_big = srv.wait(big, 60.0).t_done_ns
+    assert max(done_small) < done_big
+    for t in small + [big]:
+        srv.release(t)
+    srv.close()
+
+
+def test_budget_is_enforced(syev3, pools):
+    A64, _ = pools
+    srv = syev3.Server(memory_budget_bytes=1 << 20, num_streams=2, chunk=1 << 10)
+    with pytest.raises(syev3.Syev3Error):
+        srv.submit(A64[:20000])  # 20000 x 96 B > 1 MiB: can never be admitted
+    ts = [srv.submit(A64[k * 5000:(k + 1) * 5000]) for k in range(12)]  # each ~0.46 MiB: two at a time
+    for t in ts:
+        assert srv.wait(t, 60.0).state == 2
+        srv.release(t)
+    st = srv.stats()
+    assert st.arena_peak <= (1 << 20) and st.completed == 12
+    srv.close()
