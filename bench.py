@@ -403,18 +403,17 @@ def run_native(args):
     ms_per_step = total_ms / args.steps
     value = ws * n * args.steps / (total_ms * 1e-3)
 
-    # End to end through the public API with host buffers: pinned H2D of the
-    # step's inputs, the solve, D2H of eigenvalues and eigenvectors.
+    # End to end through the C ABI's host entry point: pinned host buffers in,
+    # the pipelined H2D copy / solve / D2H copy of eigenvalues and
+    # eigenvectors inside the timed region (the call returns when the host
+    # outputs are written).
     A_host = torch.from_numpy(A_np).pin_memory()
     lam_host = torch.empty((n, 3), dtype=torch.float64).pin_memory()
     U_host = torch.empty((n, 3, 3), dtype=torch.float64).pin_memory()
     e2e_steps = max(3, min(args.steps, 10))
 
     def e2e_step():
-        A.copy_(A_host, non_blocking=True)
-        syev3.syev3_batched(A, out=(lam, U), stream=stream)
-        lam_host.copy_(lam, non_blocking=True)
-        U_host.copy_(U, non_blocking=True)
+        syev3.syev3_batched_host(A_host, lam_host, U_host, stream=stream)
 
     e2e_ms, _ = _timed(e2e_step, e2e_steps, 1, stream, barrier)
     if ws > 1:
@@ -448,7 +447,8 @@ def run_native(args):
             "roofline": roofline,
             "gpu_launches": args.steps,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 48,
-                    "d2h_bytes_per_step": n * 96},
+                    "d2h_bytes_per_step": n * 96, "api": "syev3_batched_host (pinned host buffers, "
+                    "3-stream copy/solve pipeline, chunks of 2^21)"},
             "clocks": clocks,
         }
         if fp32 is not None:

@@ -115,6 +115,21 @@ int syev3_batched_ex(const void* A_packed6, int64_t n, void* lambda, void* U, in
 int syev3_batched_bwd(const void* lambda, const void* U, const void* g_lambda, const void* g_U, int64_t n,
                       void* g_A_packed6, double gap_tau, int dtype, syev3_stream_t stream);
 
+/* syev3_batched_host -- syev3_batched for buffers in host memory
+ * (blocking).  The batch is cut into chunks of `chunk` matrices (<= 0:
+ * 2^21); each chunk is copied in, solved and copied out on one of three
+ * library streams, so copies overlap the solves of neighbouring chunks.
+ *   A_host      : host, n x 6 of dtype (page-locked memory lets the copies
+ *                 run asynchronously; pageable memory works, slower).
+ *   lambda_host : host, n x 3, written.  U_host: host, n x 9, or NULL.
+ *   stream      : the pipeline starts after the work queued on it.
+ * Device staging buffers (3 x chunk records) are allocated by the library
+ * on the first call for a device and kept for later calls; they grow when
+ * a larger chunk is asked for.  Calls for the same device from several host
+ * threads are serialised.  Returns when the host outputs are written. */
+int syev3_batched_host(const void* A_host, int64_t n, void* lambda_host, void* U_host, int dtype, int64_t chunk,
+                       syev3_stream_t stream);
+
 /* Device-side status bits of the current device, OR-ed over all launches
  * since the last call, then cleared (synchronises the device).
  *   bit 0: a bulk-copy wait timed out (SYEV3_ETIMEOUT). */

@@ -1,0 +1,106 @@
+// host_pipeline.cpp -- syev3_batched_host: the batched solve for matrices in
+// host memory.  The batch is cut into chunks; chunk i goes to stream i % 3:
+// copy in (H2D), solve (syev3_batched), copy the eigenvalues and vectors out
+// (D2H).  With three streams, each with its own staging buffer, the copies of
+// one chunk overlap the solve of the next.  Staging buffers are device
+// memory owned by the library, allocated once per device (and grown when a
+// larger chunk is asked for), then reused by every call.
+
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/syev3.h"
+
+namespace {
+
+constexpr int kStreams = 3;
+
+constexpr int kMaxDevices = 64;
+
+struct Staging {
+  std::mutex mu;                // one pipeline per device at a time
+  size_t bytes = 0;             // per stream
+  char* buf[kStreams] = {};
+  cudaStream_t st[kStreams] = {};
+  cudaEvent_t start = nullptr;
+};
+
+Staging g_staging[kMaxDevices];
+
+int host_fail(cudaError_t e) {
+  (void)e;
+  cudaGetLastError();
+  return SYEV3_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int syev3_batched_host(const void* A_host, int64_t n, void* lambda_host, void* U_host, int dtype, int64_t chunk,
+                       syev3_stream_t stream) {
+  if (n < 0 || (dtype != SYEV3_F64 && dtype != SYEV3_F32 && dtype != SYEV3_F32_COMPENSATED)) return SYEV3_EINVAL;
+  if (n == 0) return SYEV3_OK;
+  if (A_host == nullptr || lambda_host == nullptr) return SYEV3_EINVAL;
+  if (chunk <= 0) chunk = (int64_t)1 << 21;
+  const size_t es = dtype == SYEV3_F64 ? 8 : 4;
+  const size_t in_b = 6 * es, lam_b = 3 * es, U_b = 9 * es;
+  const size_t lam_off = (size_t)chunk * in_b, U_off = lam_off + ((size_t)chunk * lam_b + 255) / 256 * 256;
+  const size_t need = U_off + (U_host ? (size_t)chunk * U_b : 0);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return host_fail(cudaErrorInvalidDevice);
+  if (dev < 0 || dev >= kMaxDevices) return SYEV3_EINVAL;
+  Staging* S = &g_staging[dev];
+  // Calls for the same device from several host threads run one after another.
+  std::lock_guard<std::mutex> hold(S->mu);
+  {
+    if (S->bytes < need) {
+      for (int k = 0; k < kStreams; ++k) {
+        if (S->buf[k]) cudaFree(S->buf[k]);
+        S->buf[k] = nullptr;
+        if (cudaMalloc(&S->buf[k], need) != cudaSuccess) {
+          S->bytes = 0;
+          return host_fail(cudaErrorMemoryAllocation);
+        }
+      }
+      S->bytes = need;
+    }
+    for (int k = 0; k < kStreams; ++k)
+      if (!S->st[k] && cudaStreamCreateWithFlags(&S->st[k], cudaStreamNonBlocking) != cudaSuccess)
+        return host_fail(cudaErrorUnknown);
+    if (!S->start && cudaEventCreateWithFlags(&S->start, cudaEventDisableTiming) != cudaSuccess)
+      return host_fail(cudaErrorUnknown);
+  }
+  // Order after the caller's stream, then run the pipeline.
+  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaEventRecord(S->start, user) != cudaSuccess) return host_fail(cudaErrorUnknown);
+  for (int k = 0; k < kStreams; ++k)
+    if (cudaStreamWaitEvent(S->st[k], S->start, 0) != cudaSuccess) return host_fail(cudaErrorUnknown);
+  const char* A = static_cast<const char*>(A_host);
+  char* L = static_cast<char*>(lambda_host);
+  char* V = static_cast<char*>(U_host);
+  int64_t i = 0;
+  for (int64_t b = 0; b < n; b += chunk, ++i) {
+    const int k = (int)(i % kStreams);
+    const int64_t cnt = (n - b) < chunk ? (n - b) : chunk;
+    char* d = S->buf[k];
+    cudaStream_t s = S->st[k];
+    if (cudaMemcpyAsync(d, A + b * in_b, cnt * in_b, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return host_fail(cudaErrorUnknown);
+    const int st = syev3_batched(d, cnt, d + lam_off, V ? d + U_off : nullptr, dtype,
+                                 reinterpret_cast<syev3_stream_t>(s));
+    if (st != SYEV3_OK) return st;
+    if (cudaMemcpyAsync(L + b * lam_b, d + lam_off, cnt * lam_b, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return host_fail(cudaErrorUnknown);
+    if (V && cudaMemcpyAsync(V + b * U_b, d + U_off, cnt * U_b, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return host_fail(cudaErrorUnknown);
+  }
+  for (int k = 0; k < kStreams; ++k)
+    if (cudaStreamSynchronize(S->st[k]) != cudaSuccess) return host_fail(cudaErrorUnknown);
+  return SYEV3_OK;
+}
+
+}  // extern "C"

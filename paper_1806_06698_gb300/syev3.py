@@ -54,6 +54,8 @@ def _load():
             lib.syev3_batched_ex.restype = i32
             lib.syev3_batched_bwd.argtypes = [vp, vp, vp, vp, i64, vp, ctypes.c_double, i32, vp]
             lib.syev3_batched_bwd.restype = i32
+            lib.syev3_batched_host.argtypes = [vp, i64, vp, vp, i32, i64, vp]
+            lib.syev3_batched_host.restype = i32
             lib.syev3_device_flags.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
             lib.syev3_device_flags.restype = i32
             _lib = lib
@@ -113,6 +115,20 @@ def syev3_batched(A6: torch.Tensor, *, vectors: bool = True, compensated: bool =
     else:
         st = lib.syev3_batched_ex(_ptr(A6), n, _ptr(lam), _ptr(U), code, _ptr(counters), _stream(stream))
     _check(st, "syev3_batched")
+    return lam, U
+
+
+def syev3_batched_host(A6: torch.Tensor, lam: torch.Tensor, U: torch.Tensor | None = None, *,
+                       compensated: bool = False, chunk: int = 1 << 21, stream=None):
+    """Blocking solve of host (CPU, ideally pinned) tensors through the C
+    ABI's pipelined host entry point; fills lam (n,3) and U (n,3,3)."""
+    for t in (A6, lam) + ((U,) if U is not None else ()):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("host buffers must be contiguous CPU tensors")
+    lib = _load()
+    st = lib.syev3_batched_host(_ptr(A6), A6.shape[0], _ptr(lam), _ptr(U), dtype_code(A6.dtype, compensated),
+                                int(chunk), _stream(stream))
+    _check(st, "syev3_batched_host")
     return lam, U
 
 

@@ -208,3 +208,29 @@ def test_near_combo_arrows(syev3):
     lam_o, U_o, info = oracle.syev3(A, with_info=True)
     assert (info[:, 0] == oracle.CLS_REDUCED).mean() > 0.5
     parity.compare_f64(A, lam, U, lam_o, U_o)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f32c"])
+def test_host_entry_point(syev3, dtype):
+    """syev3_batched_host on pinned and pageable host buffers, several
+    chunks and a ragged last chunk, equals the device entry point bit for bit."""
+    n = 50_000
+    if dtype == "f64":
+        A = inputs.mixed(n, seed=901)[0]
+    else:
+        A = inputs.mixed_fp32(n, seed=902)[0]
+    comp = dtype == "f32c"
+    At = torch.from_numpy(A)
+    lam_d, U_d = syev3.syev3_batched(At.cuda(), compensated=comp)
+    torch.cuda.synchronize()
+    for pinned in (True, False):
+        Ah = At.pin_memory() if pinned else At.clone()
+        lam = torch.empty((n, 3), dtype=At.dtype)
+        U = torch.empty((n, 3, 3), dtype=At.dtype)
+        if pinned:
+            lam, U = lam.pin_memory(), U.pin_memory()
+        syev3.syev3_batched_host(Ah, lam, U, compensated=comp, chunk=7_000)
+        assert torch.equal(lam, lam_d.cpu()) and torch.equal(U, U_d.cpu())
+    lam0 = torch.empty((n, 3), dtype=At.dtype)
+    syev3.syev3_batched_host(At, lam0, None, compensated=comp)
+    assert torch.equal(lam0, lam_d.cpu())
