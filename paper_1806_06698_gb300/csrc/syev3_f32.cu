@@ -158,68 +158,70 @@ __device__ __forceinline__ Lane32 make_lane32(const float a_in[6]) {
   return L;
 }
 
-// Borges-Gragg in FP32 for mu and nu together (Sec. 1.4.1), started by
-// f64::start32 (Eq. (7), or the small-root model); stops when
-// f/f' < C eps32 x, when f <= 0 or when a step no longer moves x.  For
-// x < ab, f = x + K - b1/x + c x/(x+ab).
+// One Borges-Gragg step in FP32 (Sec. 1.4.1) from x: returns x_{j+1}, or x
+// itself when f(x) <= 0 (at or past the root: rounding level).  For x < ab,
+// f = x + K - b1/x + c x/(x+ab) (the cancellation-free form); x_{j+1} is
+// x - Delta (Eq. (6)), or the zero of phi_j taken directly when Delta >= x/2.
+// *fx receives f(x).
+__device__ __forceinline__ float bg_step32(const float ab, const float b1, const float b2, const float g,
+                                          const float c, const float K, const float x, float* fx) {
+  const float r1 = rcp32(x), r2 = rcp32(x + ab);
+  const float t1 = b1 * r1, t2 = b2 * r2;
+  const bool small = x < ab;
+  const float f = ((x + (small ? K : -g)) - t1) + (small ? c * x * r2 : -t2);
+  *fx = f;
+  const float fp = fmaf(t2, r2, fmaf(t1, r1, 1.f));
+  const float w0 = fmaf(t2 * ab, r2 * r2, 1.f);
+  const float rb = rcp32(fmaf(f, r1, fp));
+  const float fr = f * rb;
+  const float z = (-4.f * w0) * (r1 * rb) * fr;
+  const float delta = 2.f * fr * rcp32(1.f + sqrt32(fmaxf(0.f, 1.f + z)));
+  float xn = x - delta;
+  if (!(delta < 0.5f * x)) {  // rare: the zero of phi_j directly
+    const float xr = x * r2;
+    const float w1 = fmaf(b2 * xr, xr * xr, b1);
+    const float sg = fmaf(w0, x, -fmaf(w1, r1, f));
+    const float rt = sqrt32(fmaf(sg, sg, 4.f * w0 * w1));
+    xn = (sg > 0.f) ? (sg + rt) * rcp32(2.f * w0) : (2.f * w1) * rcp32(rt - sg);
+  }
+  return (f > 0.f && xn < x) ? xn : x;
+}
+
+// mu and nu in FP32 on a fixed schedule: from the start of f64::start32 two
+// Borges-Gragg steps for both problems, straight-line (no lane leaves
+// early, so the warp stays converged).  From these starts two steps reach
+// FP32 accuracy for most problems (cubic convergence); more[k] marks a
+// problem whose second step still moved x by more than 2^-16 x, or whose
+// small-root start turned out left of the root: the kernel finishes those
+// on a compacted work list with roots32_more.
 __device__ __forceinline__ void roots32(const float ab, const float b1[2], const float b2[2], const float g[2],
-                                        const float c[2], const float K[2], float x[2], bool& capped) {
-  bool live[2], model[2];
-  float x7[2];
+                                        const float c[2], const float K[2], float x[2], bool more[2]) {
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    x[k] = f64::start32(ab, b1[k], b2[k], g[k], c[k], K[k], x7[k], model[k]);
-    live[k] = true;
+    float f0, f1, x7;
+    bool model;
+    const float x0 = f64::start32(ab, b1[k], b2[k], g[k], c[k], K[k], x7, model);
+    float x1 = bg_step32(ab, b1[k], b2[k], g[k], c[k], K[k], x0, &f0);
+    const bool restart = model && !(f0 > 0.f);  // the small-root start was not right of the root
+    if (restart) x1 = x7;
+    const float x2 = bg_step32(ab, b1[k], b2[k], g[k], c[k], K[k], x1, &f1);
+    more[k] = restart || (x1 - x2) > 0x1p-16f * x2;
+    x[k] = x2;
   }
-  capped = false;
-#pragma unroll 1
-  for (int it = 0; it <= kMaxIt32 && (live[0] || live[1]); ++it) {
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      if (!live[k]) continue;
-      const float r1 = rcp32(x[k]), r2 = rcp32(x[k] + ab);
-      const float t1 = b1[k] * r1, t2 = b2[k] * r2;
-      const bool small = x[k] < ab;
-      const float f = ((x[k] + (small ? K[k] : -g[k])) - t1) + (small ? c[k] * x[k] * r2 : -t2);
-      const float fp = fmaf(t2, r2, fmaf(t1, r1, 1.f));
-      if (model[k]) {  // first evaluation at the small-root start: keep it only if right of the root
-        model[k] = false;
-        if (!(f > 0.f)) {
-          x[k] = x7[k];
-          continue;
-        }
-      }
-      if (!(f > 0.f) || f < (kCTerm32 * kEps32) * x[k] * fp) {
-        live[k] = false;
-        continue;
-      }
-      if (it == kMaxIt32) {
-        capped = true;
-        live[k] = false;
-        continue;
-      }
-      const float w0 = fmaf(t2 * ab, r2 * r2, 1.f);
-      const float rb = rcp32(fmaf(f, r1, fp));
-      const float fr = f * rb;
-      const float z = (-4.f * w0) * (r1 * rb) * fr;
-      const float delta = 2.f * fr * rcp32(1.f + sqrt32(fmaxf(0.f, 1.f + z)));
-      float xn;
-      if (delta < 0.5f * x[k]) {
-        xn = x[k] - delta;
-      } else {  // the zero of phi_j directly (see the FP64 solver)
-        const float xr = x[k] * r2;
-        const float w1 = fmaf(b2[k] * xr, xr * xr, b1[k]);
-        const float sg = fmaf(w0, x[k], -fmaf(w1, r1, f));
-        const float rt = sqrt32(fmaf(sg, sg, 4.f * w0 * w1));
-        xn = (sg > 0.f) ? (sg + rt) * rcp32(2.f * w0) : (2.f * w1) * rcp32(rt - sg);
-      }
-      if (!(xn < x[k])) {
-        live[k] = false;
-        continue;
-      }
-      x[k] = xn;
-    }
+}
+
+// Further steps for one problem until f/f' < C eps32 x (Sec. 1.4.1), f <= 0
+// or a stalled step; returns false if kMaxIt32 steps were not enough.
+__device__ bool roots32_more(const float ab, const float b1, const float b2, const float g, float* x) {
+  const float c = b2 * rcp32(ab), K = -g - c;
+  for (int it = 0; it < kMaxIt32; ++it) {
+    float f;
+    const float xn = bg_step32(ab, b1, b2, g, c, K, *x, &f);
+    const bool go = f > (kCTerm32 * kEps32) * (*x) && xn < *x;
+    *x = xn;
+    if (!go) return true;
   }
+  return false;
 }
 
 // Double-float value of the spectral function at x (FP32 data exact), and
@@ -300,18 +302,19 @@ __device__ __forceinline__ void finish32(const Lane32& L, float mu, float nu, fl
   float x00 = x[0][0], x01 = x[0][1], x02 = x[0][2];
   float x10 = x[1][0], x11 = x[1][1], x12 = x[1][2];
   float x20 = x[2][0], x21 = x[2][1], x22 = x[2][2];
-#define SYEV3_CSWAP32(la, a0, a1_, a2_, lb, b0, b1_, b2_) \
-  if (lb < la) {                                         \
-    float t_;                                            \
-    t_ = la; la = lb; lb = t_;                           \
-    t_ = a0; a0 = b0; b0 = t_;                           \
-    t_ = a1_; a1_ = b1_; b1_ = t_;                       \
-    t_ = a2_; a2_ = b2_; b2_ = t_;                       \
-  }
-  SYEV3_CSWAP32(l0, x00, x01, x02, l1, x10, x11, x12)
-  SYEV3_CSWAP32(l1, x10, x11, x12, l2, x20, x21, x22)
-  SYEV3_CSWAP32(l0, x00, x01, x02, l1, x10, x11, x12)
-#undef SYEV3_CSWAP32
+  // Ascending and stable: three compare-and-swap steps with strict "<",
+  // written as selects so that no lane branches.
+  auto cswap = [](float& la, float& a0, float& a1_, float& a2_, float& lb, float& b0, float& b1_, float& b2_) {
+    const bool sw = lb < la;
+    const float tl = la, t0 = a0, t1 = a1_, t2 = a2_;
+    la = sw ? lb : la;   lb = sw ? tl : lb;
+    a0 = sw ? b0 : a0;   b0 = sw ? t0 : b0;
+    a1_ = sw ? b1_ : a1_; b1_ = sw ? t1 : b1_;
+    a2_ = sw ? b2_ : a2_; b2_ = sw ? t2 : b2_;
+  };
+  cswap(l0, x00, x01, x02, l1, x10, x11, x12);
+  cswap(l1, x10, x11, x12, l2, x20, x21, x22);
+  cswap(l0, x00, x01, x02, l1, x10, x11, x12);
   const float ls[3] = {l0, l1, l2};
   const float xs[3][3] = {{x00, x01, x02}, {x10, x11, x12}, {x20, x21, x22}};
 #pragma unroll
@@ -343,6 +346,10 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
   __shared__ float s_fa[kComp ? 9 * kTPB : 1];
   __shared__ int s_fi[kComp ? 2 * kTPB : 1];
   __shared__ int s_nflag;
+  // Roots that need more steps than the fixed schedule: (ab, b1, b2, g, x).
+  __shared__ float s_more[2 * kTPB * 5];
+  __shared__ bool s_more_capped[2 * kTPB];
+  __shared__ int s_nmore;
   __shared__ alignas(8) uint64_t s_bar[2];
 
   const int tid = threadIdx.x, lane_id = tid & 31;
@@ -354,6 +361,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
 
   if (tid == 0) {
     s_nflag = 0;
+    s_nmore = 0;
     if (kBulkIn) {
       mbar_init(&s_bar[0], 1);
       mbar_init(&s_bar[1], 1);
@@ -414,15 +422,55 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
     // Roots (Sec. 1.2): problem 0 is mu, problem 1 is nu (spikes swapped).
     float root[2] = {0.f, 0.f};
     bool capped = false;
+    bool more[2] = {false, false};
+    float ab = 0.f, pb1[2] = {0.f, 0.f}, pb2[2] = {0.f, 0.f}, pg[2] = {0.f, 0.f};
     if (L.cls == kRed) {
-      const float ab = L.a1 - L.a2;
+      ab = L.a1 - L.a2;
       const float bb1 = L.b1 * L.b1, bb2 = L.b2 * L.b2;
-      const float pb1[2] = {bb1, bb2}, pb2[2] = {bb2, bb1};
-      const float pg[2] = {L.g - L.a1, L.a2 - L.g};
+      pb1[0] = bb1; pb1[1] = bb2; pb2[0] = bb2; pb2[1] = bb1;
+      pg[0] = L.g - L.a1; pg[1] = L.a2 - L.g;
       const float rab = rcp32(ab);
       const float pc[2] = {pb2[0] * rab, pb2[1] * rab};
       const float pK[2] = {-pg[0] - pc[0], -pg[1] - pc[1]};
-      roots32(ab, pb1, pb2, pg, pc, pK, root, capped);
+      roots32(ab, pb1, pb2, pg, pc, pK, root, more);
+    }
+    // Problems that need more steps: compacted with warp ballots into a
+    // shared work list and finished with every lane of the CTA available.
+    {
+      const unsigned m0 = __ballot_sync(0xffffffffu, more[0]);
+      const unsigned m1 = __ballot_sync(0xffffffffu, more[1]);
+      int slot[2] = {-1, -1};
+      const int total = __popc(m0) + __popc(m1);
+      int wbase = 0;
+      if (lane_id == 0 && total) wbase = atomicAdd(&s_nmore, total);
+      wbase = __shfl_sync(0xffffffffu, wbase, 0);
+      if (more[0]) slot[0] = wbase + __popc(m0 & lt_mask);
+      if (more[1]) slot[1] = wbase + __popc(m0) + __popc(m1 & lt_mask);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (slot[k] >= 0) {
+          float* w = &s_more[slot[k] * 5];
+          w[0] = ab; w[1] = pb1[k]; w[2] = pb2[k]; w[3] = pg[k]; w[4] = root[k];
+        }
+      }
+      __syncthreads();
+      const int nm = s_nmore;
+      for (int i = tid; i < nm; i += kTPB) {
+        float* w = &s_more[i * 5];
+        float x = w[4];
+        s_more_capped[i] = !roots32_more(w[0], w[1], w[2], w[3], &x);
+        w[4] = x;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (slot[k] >= 0) {
+          root[k] = s_more[slot[k] * 5 + 4];
+          capped |= s_more_capped[slot[k]];
+        }
+      }
+    }
+    if (L.cls == kRed) {
       if (kComp) {
         // Exact FP32 data as double-float, then one Newton correction with
         // a double-float f at each root.
@@ -536,7 +584,10 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
       }
     }
     __syncthreads();
-    if (tid == 0) s_nflag = 0;
+    if (tid == 0) {
+      s_nflag = 0;
+      s_nmore = 0;
+    }
 
     {
       float* dst = lam_out + base * 3;
