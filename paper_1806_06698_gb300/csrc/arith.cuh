@@ -37,6 +37,16 @@ __device__ __forceinline__ float rsqrt32(float x) {
 // 2^k for -1022 <= k <= 1023, built from its exponent field.
 __device__ __forceinline__ double pow2(int k) { return __hiloint2double((k + 1023) << 20, 0); }
 
+// |x| as an unsigned integer that orders like |x| (any non-NaN x).
+__device__ __forceinline__ uint64_t mag_bits(double x) {
+  return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+// x with its sign bit XOR-ed with bit 31 of `flip` (0 or 0x80000000).
+__device__ __forceinline__ double flip_sign(double x, int flip) {
+  return __hiloint2double(__double2hiint(x) ^ flip, __double2loint(x));
+}
+
 // 2^k as a float for -126 <= k <= 127.
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
 

@@ -410,16 +410,16 @@ __device__ __forceinline__ void finish_lane(const Lane& L, double mu, double nu,
   const double xs[3][3] = {{x00, x01, x02}, {x10, x11, x12}, {x20, x21, x22}};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const double y0 = xs[k][0], y1 = xs[k][1], y2 = xs[k][2];
-    // Largest-magnitude component positive, first one on ties.
-    double big = y0;
-    if (fabs(y1) > fabs(big)) big = y1;
-    if (fabs(y2) > fabs(y0) && fabs(y2) > fabs(y1)) big = y2;
-    const double sg = (big < 0.0) ? -1.0 : 1.0;
     lam[k] = (L.unscale != 0.0) ? ls[k] * L.unscale : scalbn(ls[k], L.e);
-    U[0 * 3 + k] = sg * y0;
-    U[1 * 3 + k] = sg * y1;
-    U[2 * 3 + k] = sg * y2;
+    // Largest-magnitude component positive, first one on ties: magnitudes
+    // compared as integers (|y| orders like its bit pattern with the sign
+    // cleared), the sign applied by flipping sign bits (no FP64 work).
+    const uint64_t m0 = mag_bits(xs[k][0]), m1 = mag_bits(xs[k][1]), m2 = mag_bits(xs[k][2]);
+    const double big = (m2 > m0 && m2 > m1) ? xs[k][2] : ((m1 > m0) ? xs[k][1] : xs[k][0]);
+    const int flip = __double2hiint(big) & (int)0x80000000;
+    U[0 * 3 + k] = flip_sign(xs[k][0], flip);
+    U[1 * 3 + k] = flip_sign(xs[k][1], flip);
+    U[2 * 3 + k] = flip_sign(xs[k][2], flip);
   }
 }
 

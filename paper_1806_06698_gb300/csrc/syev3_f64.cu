@@ -48,8 +48,14 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
   __shared__ alignas(16) double s_U[kTPB * 9];
   // Work list of roots left for the full FP64 iteration: up to two per lane.
   __shared__ double s_hx[2 * kTPB], s_hab[2 * kTPB], s_hb1[2 * kTPB], s_hb2[2 * kTPB], s_hg[2 * kTPB];
+  __shared__ bool s_hcap[2 * kTPB];
   __shared__ int s_nhard;
+  // Class reorder of a tile: Lane records by slot (struct of arrays), held
+  // in s_U, which is free until phase E; owner = the matrix's row in the tile.
+  __shared__ int s_pe[kTPB], s_pmeta[kTPB];
+  __shared__ int s_nred, s_noth;
   __shared__ alignas(8) uint64_t s_bar[2];
+  double* const s_perm = s_U;  // 8 * kTPB doubles: a1 a2 b1 b2 g c s unscale
 
   const int tid = threadIdx.x, lane_id = tid & 31;
   const unsigned lt_mask = (1u << lane_id) - 1u;
@@ -60,6 +66,8 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
 
   if (tid == 0) {
     s_nhard = 0;
+    s_nred = 0;
+    s_noth = 0;
     if (kBulkIn) {
       mbar_init(&s_bar[0], 1);
       mbar_init(&s_bar[1], 1);
@@ -103,15 +111,63 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
       __syncthreads();
     }
 
-    // Phase A: arrow and class.
+    // Phase A: arrow and class of the thread's own matrix.
     Lane L;
-    L.cls = kIdle;
-    if (tid < cnt) {
-      const double2* src = reinterpret_cast<const double2*>(&s_in[buf][tid * 6]);
-      const double2 p0 = src[0], p1 = src[1], p2 = src[2];
-      const double a[6] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y};
-      L = make_lane(a);
+    {
+      Lane A0;
+      A0.cls = kIdle;
+      if (tid < cnt) {
+        const double2* src = reinterpret_cast<const double2*>(&s_in[buf][tid * 6]);
+        const double2 p0 = src[0], p1 = src[1], p2 = src[2];
+        const double a[6] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y};
+        A0 = make_lane(a);
+      }
+      // Reorder by class: reduced arrows take slots 0, 1, ... and the other
+      // classes slots cnt-1, cnt-2, ..., so that the warps below run either
+      // the zero finder and the Sec. 1.2 vectors or the short paths, not
+      // both with a few lanes active.  Thread t then finishes slot t.
+      const bool red = (A0.cls == kReduced);
+      const bool oth = (A0.cls != kReduced) && (A0.cls != kIdle);
+      const unsigned mr = __ballot_sync(0xffffffffu, red);
+      const unsigned mo = __ballot_sync(0xffffffffu, oth);
+      int rb = 0, ob = 0;
+      if (lane_id == 0) {
+        if (mr) rb = atomicAdd(&s_nred, __popc(mr));
+        if (mo) ob = atomicAdd(&s_noth, __popc(mo));
+      }
+      rb = __shfl_sync(0xffffffffu, rb, 0);
+      ob = __shfl_sync(0xffffffffu, ob, 0);
+      int slot = -1;
+      if (red) slot = rb + __popc(mr & lt_mask);
+      if (oth) slot = cnt - 1 - (ob + __popc(mo & lt_mask));
+      if (slot >= 0) {
+        s_perm[0 * kTPB + slot] = A0.a1;
+        s_perm[1 * kTPB + slot] = A0.a2;
+        s_perm[2 * kTPB + slot] = A0.b1;
+        s_perm[3 * kTPB + slot] = A0.b2;
+        s_perm[4 * kTPB + slot] = A0.g;
+        s_perm[5 * kTPB + slot] = A0.c;
+        s_perm[6 * kTPB + slot] = A0.s;
+        s_perm[7 * kTPB + slot] = A0.unscale;
+        s_pe[slot] = A0.e;
+        s_pmeta[slot] = tid | (A0.cls << 8);
+      }
+      __syncthreads();
+      L.cls = kIdle;
+      if (tid < cnt) {
+        L.a1 = s_perm[0 * kTPB + tid];
+        L.a2 = s_perm[1 * kTPB + tid];
+        L.b1 = s_perm[2 * kTPB + tid];
+        L.b2 = s_perm[3 * kTPB + tid];
+        L.g = s_perm[4 * kTPB + tid];
+        L.c = s_perm[5 * kTPB + tid];
+        L.s = s_perm[6 * kTPB + tid];
+        L.unscale = s_perm[7 * kTPB + tid];
+        L.e = s_pe[tid];
+        L.cls = s_pmeta[tid] >> 8;
+      }
     }
+    const int owner = (tid < cnt) ? (s_pmeta[tid] & 0xff) : tid;
 
     // Phases B, C: FP32 seeds, then one FP64 step and the stopping test.
     // Problem 0 is mu (A - a1 I), problem 1 is nu (P(a2 I - A)P: spikes
@@ -176,16 +232,20 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
     }
     __syncthreads();
     const int n_hard = s_nhard;
-    bool capped = false;
     for (int i = tid; i < n_hard; i += kTPB) {
       bool cp;
       s_hx[i] = zero_bg_full(s_hab[i], s_hb1[i], s_hb2[i], s_hg[i], s_hx[i], cp);
-      capped |= cp;
+      s_hcap[i] = cp;
     }
     __syncthreads();
+    bool capped = false;
 #pragma unroll
-    for (int k = 0; k < 2; ++k)
-      if (slot[k] >= 0) root[k] = s_hx[slot[k]];
+    for (int k = 0; k < 2; ++k) {
+      if (slot[k] >= 0) {
+        root[k] = s_hx[slot[k]];
+        capped |= s_hcap[slot[k]];
+      }
+    }
 
     // Phase E: eigenpairs, staged for the write-back.
     bool nonfinite = false;
@@ -202,9 +262,9 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
         finish_lane(L, root[0], root[1], lam, U);
       }
 #pragma unroll
-      for (int k = 0; k < 3; ++k) s_lam[tid * 3 + k] = lam[k];
+      for (int k = 0; k < 3; ++k) s_lam[owner * 3 + k] = lam[k];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) s_U[tid * 9 + k] = U[k];
+      for (int k = 0; k < 9; ++k) s_U[owner * 9 + k] = U[k];
     }
     if (counters != nullptr) {
       const unsigned cm = __ballot_sync(0xffffffffu, capped);
@@ -215,7 +275,11 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
       }
     }
     __syncthreads();
-    if (tid == 0) s_nhard = 0;
+    if (tid == 0) {
+      s_nhard = 0;
+      s_nred = 0;
+      s_noth = 0;
+    }
 
     // Coalesced write-back of the tile: 16-byte stores where aligned.
     {
