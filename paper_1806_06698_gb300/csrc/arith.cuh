@@ -1,6 +1,7 @@
 // arith.cuh -- arithmetic primitives of the eigensolver kernels (sm_103a).
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 
 namespace syev3 {
@@ -36,6 +37,35 @@ __device__ __forceinline__ float rsqrt32(float x) {
 
 // 2^k for -1022 <= k <= 1023, built from its exponent field.
 __device__ __forceinline__ double pow2(int k) { return __hiloint2double((k + 1023) << 20, 0); }
+
+// Comparisons of doubles whose signs are known, on the integer pipes (the
+// FP64 pipe is the scarce one).  For x, y >= +0, not NaN, x < y exactly when
+// their bit patterns compare so as unsigned integers; against 2^k (low word
+// zero) the high words alone decide.  x > 0 for a non-NaN x is a signed
+// comparison of the pattern with 0.
+__device__ __forceinline__ uint64_t dbits(double x) { return (uint64_t)__double_as_longlong(x); }
+
+// High word of 2^k, -1022 <= k <= 1023.
+__host__ __device__ constexpr unsigned hi_pow2(int k) { return (unsigned)(k + 1023) << 20; }
+
+// High word of |x|.
+__device__ __forceinline__ unsigned hi_mag(double x) { return (unsigned)__double2hiint(x) & 0x7fffffffu; }
+
+// x > 0 (x not NaN).
+__device__ __forceinline__ bool is_pos(double x) { return __double_as_longlong(x) > 0; }
+
+// x == +0 or -0.
+__device__ __forceinline__ bool is_zero(double x) { return (dbits(x) << 1) == 0; }
+
+// x * 2^k by exponent arithmetic for x >= 2^-1022 in magnitude (normal) when
+// the result is normal too; otherwise scalbn.  Zero stays zero.
+__device__ __forceinline__ double mul_pow2(double x, int k) {
+  const int h = __double2hiint(x);
+  const int ne = ((h >> 20) & 0x7ff) + k;
+  if (((h >> 20) & 0x7ff) != 0 && ne >= 1 && ne <= 2046) return __hiloint2double(h + k * (1 << 20), __double2loint(x));
+  if (is_zero(x)) return x;
+  return scalbn(x, k);
+}
 
 // |x| as an unsigned integer that orders like |x| (any non-NaN x).
 __device__ __forceinline__ uint64_t mag_bits(double x) {

@@ -23,7 +23,7 @@ constexpr int kSeedIt = 16;      // FP32 seeding step cap
 constexpr double kEps = 0x1p-52;
 constexpr double kCDefl = 1.0;   // C of the deflation test (Sec. 1.1)
 constexpr double kCTerm = 2.0;   // C of the stopping rule (Sec. 1.4.1)
-constexpr double kTinySpike = 0x1p-480;  // spikes below this are zeroed (beta-deflation)
+constexpr int kTinySpikeExp = -480;  // spikes below 2^-480 are zeroed (beta-deflation)
 constexpr float kEps32 = 0x1p-23f;
 
 constexpr int kDiagonal = 0, kDeflated = 1, kReduced = 2, kNonFinite = 3, kIdle = 4;
@@ -41,7 +41,7 @@ struct Rot {
 
 __device__ __forceinline__ Rot ordered_rotation(double p, double q, double r) {
   Rot J;
-  if (q == 0.0) {
+  if (is_zero(q)) {
     const bool keep = p >= r;
     J.c = keep ? 1.0 : 0.0;
     J.s = keep ? 0.0 : 1.0;
@@ -53,7 +53,7 @@ __device__ __forceinline__ Rot ordered_rotation(double p, double q, double r) {
   const double rad = sqrt(fma(D, D, q2 * q2));  // 2 hypot(d, q)
   const double den = fabs(D) + rad;
   double t;
-  if (den >= 0x1p-1000)
+  if (hi_mag(den) >= hi_pow2(-1000))  // den >= 2^-1000 (den >= 0)
     t = q2 * rcp64(den);
   else
     t = (den > 0.0) ? q2 / den : copysign(1.0, q);
@@ -176,24 +176,28 @@ __device__ __forceinline__ void seed32x2(const float ab, const float b1[2], cons
 // the root.
 __device__ __forceinline__ int finish64(const double ab, const double b1, const double b2, const double g,
                                         const double c, const double K, double& x) {
-  const bool small = x < ab;  // choice of the evaluation form (see above)
+  // x >= 2^-900 and ab >= 2^-100 (checked by the caller): every quantity
+  // compared below is a normal positive number or a finite f, so the
+  // comparisons run on bit patterns (see arith.cuh).
+  const bool small = dbits(x) < dbits(ab);  // x < ab: choice of the evaluation form (see above)
   const double lead = small ? K : -g;
   double r1 = rcp64(x), r2 = rcp64(x + ab);
   double t1 = b1 * r1, t2 = b2 * r2;
   double f = ((x + lead) - t1) + (small ? c * x * r2 : -t2);
   double fp = fma(t2, r2, fma(t1, r1, 1.0));  // Eq. (3)
-  if (!(f > 0.0)) return 2;
+  if (!is_pos(f)) return 2;
   const double w0 = fma(t2 * ab, r2 * r2, 1.0);  // omega_0
   const double rb = rcp64(fma(f, r1, fp));       // 1/b, b = f' + f/x
   const double fr = f * rb;                      // q/2 = f/b
   const double z = (-4.0 * w0) * (r1 * rb) * fr; // (2a/b) q, a = -omega_0/x
   // Delta = q/(1 + sqrt(1+z)) = fr * S(z); S = 2/(1+sqrt(1+z)) = 1 - z/4 + z^2/8 - ...
-  const double S = (fabs(z) < 0x1p-12) ? fma(z, fma(z, 0.125, -0.25), 1.0)
-                                       : 2.0 / (1.0 + sqrt(fmax(0.0, 1.0 + z)));
+  const double S = (hi_mag(z) < hi_pow2(-12)) ? fma(z, fma(z, 0.125, -0.25), 1.0)
+                                              : 2.0 / (1.0 + sqrt(fmax(0.0, 1.0 + z)));
   const double delta = fr * S;
-  if (!(delta < 0.5 * x)) return 1;  // zero of phi_j far below x: leave it to the full iteration
+  // delta >= x/2: the zero of phi_j is far below x; leave it to the full iteration.
+  if (dbits(delta) >= dbits(x) - (1ull << 52)) return 1;
   const double xn = x - delta;
-  if (!(xn < x)) return 0;  // the step no longer moves x: rounding level
+  if (!(dbits(xn) < dbits(x))) return 0;  // the step no longer moves x: rounding level
   x = xn;
   r1 = rcp64(x);
   r2 = rcp64(x + ab);
@@ -201,8 +205,9 @@ __device__ __forceinline__ int finish64(const double ab, const double b1, const 
   t2 = b2 * r2;
   f = ((x + lead) - t1) + (small ? c * x * r2 : -t2);
   fp = fma(t2, r2, fma(t1, r1, 1.0));
-  if (!(f > 0.0)) return 0;                       // at or past the root: rounding level
-  if (f < (kCTerm * kEps) * x * fp) return 0;     // f/f' < C eps x
+  if (!is_pos(f)) return 0;  // at or past the root: rounding level
+  // f/f' < C eps x with C eps = 2^-51: f < 2^-51 (x f'), the product normal.
+  if (dbits(f) < dbits(x * fp) - (51ull << 52)) return 0;
   return 1;
 }
 
@@ -273,8 +278,7 @@ __device__ double zero_bg_full(double ab, double b1, double b2, double g, double
 
 struct Lane {
   double a1, a2, b1, b2, g, c, s;  // ordered arrow and its rotation (pre-scaled frame)
-  double unscale;                  // 2^e (fast path), or 0 -> use scalbn(., e)
-  int e;
+  int e;                           // input = 2^e x pre-scaled frame
   int cls;
 };
 
@@ -293,15 +297,23 @@ __device__ __forceinline__ Lane make_lane(const double a_in[6]) {
     L.cls = kNonFinite;
     return L;
   }
-  // Exact power-of-two pre-scale: the largest entry lands in [0.5, 1).
+  // Exact power-of-two pre-scale: the largest entry lands in [0.5, 1).  When
+  // every entry is zero or stays normal, by exponent arithmetic; otherwise
+  // (subnormal results or inputs, huge entries) by scalbn.
   double a[6];
-  if (E >= 1 && E <= 2044) {
-    L.e = E - 1022;
-    const double sc = pow2(-L.e);
+  L.e = E - 1022;
+  bool exp_ok = (E >= 1 && E <= 2044);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) a[i] = a_in[i] * sc;
-    L.unscale = pow2(L.e);
-  } else {  // zero, subnormal or huge entries
+  for (int i = 0; i < 6; ++i) {
+    const int ex = (__double2hiint(a_in[i]) >> 20) & 0x7ff;
+    exp_ok &= is_zero(a_in[i]) || (ex >= 1 && ex - L.e >= 1);
+  }
+  if (exp_ok) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+      a[i] = is_zero(a_in[i]) ? a_in[i]
+                              : __hiloint2double(__double2hiint(a_in[i]) - L.e * (1 << 20), __double2loint(a_in[i]));
+  } else {
     double amax = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) amax = fmax(amax, fabs(a_in[i]));
@@ -310,7 +322,6 @@ __device__ __forceinline__ Lane make_lane(const double a_in[6]) {
     L.e = e;
 #pragma unroll
     for (int i = 0; i < 6; ++i) a[i] = scalbn(a_in[i], -e);
-    L.unscale = 0.0;
   }
   const Rot J = ordered_rotation(a[0], a[3], a[1]);
   L.a1 = J.l1;
@@ -320,15 +331,17 @@ __device__ __forceinline__ Lane make_lane(const double a_in[6]) {
   L.g = a[2];
   double b1 = fma(J.c, a[4], J.s * a[5]);
   double b2 = fma(J.c, a[5], -J.s * a[4]);
-  if (fabs(b1) < kTinySpike) b1 = 0.0;  // exact beta-deflation of a negligible spike
-  if (fabs(b2) < kTinySpike) b2 = 0.0;
+  // Exact beta-deflation of a negligible spike (|b| < 2^kTinySpikeExp).
+  if (hi_mag(b1) < hi_pow2(kTinySpikeExp)) b1 = 0.0;
+  if (hi_mag(b2) < hi_pow2(kTinySpikeExp)) b2 = 0.0;
   L.b1 = b1;
   L.b2 = b2;
   const double abar = L.a1 - L.a2;
   const double h2 = fma(b1, b1, b2 * b2);
-  if (h2 == 0.0)
+  // Both sides of the deflation test are >= +0: compared as bit patterns.
+  if (dbits(h2) == 0)
     L.cls = kDiagonal;
-  else if (fabs(abar * b1 * b2) <= (kCDefl * kEps) * fabs(L.a1 + L.a2) * h2)
+  else if (dbits(fabs(abar * b1 * b2)) <= dbits((kCDefl * kEps) * fabs(L.a1 + L.a2) * h2))
     L.cls = kDeflated;  // also the exact beta- and combo-deflations
   else
     L.cls = kReduced;
@@ -373,7 +386,7 @@ __device__ __forceinline__ void finish_lane(const Lane& L, double mu, double nu,
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       double ss = fma(v[k][0], v[k][0], fma(v[k][1], v[k][1], v[k][2] * v[k][2]));
-      if (!(ss >= 0x1p-1000)) {
+      if (hi_mag(ss) < hi_pow2(-1000)) {  // ss < 2^-1000 (ss >= 0)
         // Squares near underflow (u2 ~ beta^3 when mu and nu are both tiny):
         // bring the largest component to [0.5, 1) by an exact power of two.
         int E = 1;
@@ -410,7 +423,7 @@ __device__ __forceinline__ void finish_lane(const Lane& L, double mu, double nu,
   const double xs[3][3] = {{x00, x01, x02}, {x10, x11, x12}, {x20, x21, x22}};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    lam[k] = (L.unscale != 0.0) ? ls[k] * L.unscale : scalbn(ls[k], L.e);
+    lam[k] = mul_pow2(ls[k], L.e);
     // Largest-magnitude component positive, first one on ties: magnitudes
     // compared as integers (|y| orders like its bit pattern with the sign
     // cleared), the sign applied by flipping sign bits (no FP64 work).

@@ -535,7 +535,6 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
         D.a1 = f[0]; D.a2 = f[1]; D.b1 = f[2]; D.b2 = f[3]; D.g = f[4]; D.c = f[5]; D.s = f[6];
         D.cls = code & 3;
         D.e = code >> 2;
-        D.unscale = (D.e >= -1022 && D.e <= 1023) ? pow2(D.e) : 0.0;
         double mu = f[7], nu = f[8];
         if (D.cls == kRed) {
           // Final FP64 Newton step on mu and nu (Sec. 1.4.2).

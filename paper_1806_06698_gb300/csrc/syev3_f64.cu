@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
   __shared__ int s_pe[kTPB], s_pmeta[kTPB];
   __shared__ int s_nred, s_noth;
   __shared__ alignas(8) uint64_t s_bar[2];
-  double* const s_perm = s_U;  // 8 * kTPB doubles: a1 a2 b1 b2 g c s unscale
+  double* const s_perm = s_U;  // 7 * kTPB doubles: a1 a2 b1 b2 g c s
 
   const int tid = threadIdx.x, lane_id = tid & 31;
   const unsigned lt_mask = (1u << lane_id) - 1u;
@@ -148,7 +148,6 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
         s_perm[4 * kTPB + slot] = A0.g;
         s_perm[5 * kTPB + slot] = A0.c;
         s_perm[6 * kTPB + slot] = A0.s;
-        s_perm[7 * kTPB + slot] = A0.unscale;
         s_pe[slot] = A0.e;
         s_pmeta[slot] = tid | (A0.cls << 8);
       }
@@ -162,7 +161,6 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
         L.g = s_perm[4 * kTPB + tid];
         L.c = s_perm[5 * kTPB + tid];
         L.s = s_perm[6 * kTPB + tid];
-        L.unscale = s_perm[7 * kTPB + tid];
         L.e = s_pe[tid];
         L.cls = s_pmeta[tid] >> 8;
       }
@@ -182,7 +180,8 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
       pb1[0] = bb1; pb2[0] = bb2; pg[0] = L.g - L.a1;
       pb1[1] = bb2; pb2[1] = bb1; pg[1] = L.a2 - L.g;
       // FP32 can carry the problem when its data are normal FP32 numbers.
-      const bool fp32_ok = bb1 >= 0x1p-100 && bb2 >= 0x1p-100 && ab >= 0x1p-100;
+      const bool fp32_ok = hi_mag(bb1) >= hi_pow2(-100) && hi_mag(bb2) >= hi_pow2(-100) &&
+                           hi_mag(ab) >= hi_pow2(-100);  // all three >= 2^-100 (all >= 0)
       float sd[2] = {0.f, 0.f};
       double pc[2] = {0.0, 0.0}, pK[2] = {0.0, 0.0};
       if (fp32_ok) {
@@ -201,7 +200,9 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
       for (int k = 0; k < 2; ++k) {
         double x = (double)sd[k];
         int st = 2;
-        if (x >= 0x1p-900 && x <= 0x1p+100) st = finish64(ab, pb1[k], pb2[k], pg[k], pc[k], pK[k], x);
+        // 2^-900 <= x <= 2^100 (x >= 0): the range finish64 assumes.
+        if (hi_mag(x) >= hi_pow2(-900) && dbits(x) <= dbits(0x1p+100))
+          st = finish64(ab, pb1[k], pb2[k], pg[k], pc[k], pK[k], x);
         root[k] = (st == 2) ? 0.0 : x;  // 0: restart from Eq. (7)
         hard[k] = (st != 0);
       }
