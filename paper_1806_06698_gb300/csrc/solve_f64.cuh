@@ -175,10 +175,12 @@ __device__ __forceinline__ void seed32x2(const float ab, const float b1[2], cons
 // right of the root (more steps needed), 2 when the start was not right of
 // the root.
 __device__ __forceinline__ int finish64(const double ab, const double b1, const double b2, const double g,
-                                        const double c, const double K, double& x) {
-  // x >= 2^-900 and ab >= 2^-100 (checked by the caller): every quantity
-  // compared below is a normal positive number or a finite f, so the
-  // comparisons run on bit patterns (see arith.cuh).
+                                        const double c, const double K, const float abf, const float b2f,
+                                        double& x) {
+  // x >= 2^-900 and ab, b1, b2 >= 2^-100 (checked by the caller; abf, b2f
+  // are ab, b2 rounded to FP32): every quantity compared below is a normal
+  // positive number or a finite f, so the comparisons run on bit patterns
+  // (see arith.cuh).
   const bool small = dbits(x) < dbits(ab);  // x < ab: choice of the evaluation form (see above)
   const double lead = small ? K : -g;
   double r1 = rcp64(x), r2 = rcp64(x + ab);
@@ -186,14 +188,23 @@ __device__ __forceinline__ int finish64(const double ab, const double b1, const 
   double f = ((x + lead) - t1) + (small ? c * x * r2 : -t2);
   double fp = fma(t2, r2, fma(t1, r1, 1.0));  // Eq. (3)
   if (!is_pos(f)) return 2;
-  const double w0 = fma(t2 * ab, r2 * r2, 1.0);  // omega_0
-  const double rb = rcp64(fma(f, r1, fp));       // 1/b, b = f' + f/x
-  const double fr = f * rb;                      // q/2 = f/b
-  const double z = (-4.0 * w0) * (r1 * rb) * fr; // (2a/b) q, a = -omega_0/x
-  // Delta = q/(1 + sqrt(1+z)) = fr * S(z); S = 2/(1+sqrt(1+z)) = 1 - z/4 + z^2/8 - ...
-  const double S = (hi_mag(z) < hi_pow2(-12)) ? fma(z, fma(z, 0.125, -0.25), 1.0)
-                                              : 2.0 / (1.0 + sqrt(fmax(0.0, 1.0 + z)));
-  const double delta = fr * S;
+  // The step of Eqs. (5), (6): Delta = (f/b) S(z) with b = f' + f/x,
+  // z = -4 omega_0 f / (x b^2) and S(z) = 2/(1 + sqrt(1 + z)).  Only f/b is
+  // needed to FP64 accuracy: an FP32 reciprocal of b and one correction give
+  // it to 2^-46.  From a start within FP32 accuracy of the root |z| is tiny
+  // and S - 1 = -z/4 + z^2/8 - ... (about z/4) is formed in FP32; a start
+  // with |z| >= 2^-12, or with b beyond FP32 range, is left to the full
+  // iteration.
+  const double b = fma(f, r1, fp);
+  if (hi_mag(b) >= hi_pow2(126)) return 1;  // b >= 2^126 (b >= 1 always)
+  const float rbf = rcp32((float)b);
+  const double q0 = f * (double)rbf;
+  const double fr = fma(fma(-b, q0, f), (double)rbf, q0);  // f/b
+  const float xf = (float)x, r1f = rcp32(xf), r2f = rcp32(xf + abf);
+  const float w0f = fmaf(b2f * r2f * abf, r2f * r2f, 1.f);  // omega_0
+  const float zf = (-4.f * w0f) * (r1f * rbf) * (float)fr;
+  if (!(fabsf(zf) < 0x1p-12f)) return 1;
+  const double delta = fma(fr, (double)(zf * fmaf(zf, 0.125f, -0.25f)), fr);
   // delta >= x/2: the zero of phi_j is far below x; leave it to the full iteration.
   if (dbits(delta) >= dbits(x) - (1ull << 52)) return 1;
   const double xn = x - delta;
@@ -380,11 +391,10 @@ __device__ __forceinline__ void finish_lane(const Lane& L, double mu, double nu,
     l[1] = (nu - mu) + g;
     l[2] = a2 - nu;
     const double mpa = mu + abar, npa = nu + abar;
-    v[0][0] = b1 * mpa;         v[0][1] = b2 * mu;         v[0][2] = mu * mpa;
-    v[1][0] = -(b2 * mu) * npa; v[1][1] = (b1 * nu) * mpa; v[1][2] = (b1 * b2) * abar;
-    v[2][0] = b1 * nu;          v[2][1] = b2 * npa;        v[2][2] = -(nu * npa);
+    v[0][0] = b1 * mpa; v[0][1] = b2 * mu;  v[0][2] = mu * mpa;
+    v[2][0] = b1 * nu;  v[2][1] = b2 * npa; v[2][2] = -(nu * npa);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 3; k += 2) {
       double ss = fma(v[k][0], v[k][0], fma(v[k][1], v[k][1], v[k][2] * v[k][2]));
       if (hi_mag(ss) < hi_pow2(-1000)) {  // ss < 2^-1000 (ss >= 0)
         // Squares near underflow (u2 ~ beta^3 when mu and nu are both tiny):
@@ -399,6 +409,13 @@ __device__ __forceinline__ void finish_lane(const Lane& L, double mu, double nu,
       const double inv = rsqrt(ss);
       v[k][0] *= inv; v[k][1] *= inv; v[k][2] *= inv;
     }
+    // The middle vector as u1 x u3 instead of its closed form: u1 and u3 are
+    // unit and orthogonal to rounding, so the product is unit without a
+    // normalisation, and its error is at most the sum of theirs, each within
+    // eps / gap of its eigenvalue <= eps / (gap of the middle eigenvalue).
+    v[1][0] = fma(v[0][1], v[2][2], -v[0][2] * v[2][1]);
+    v[1][1] = fma(v[0][2], v[2][0], -v[0][0] * v[2][2]);
+    v[1][2] = fma(v[0][0], v[2][1], -v[0][1] * v[2][0]);
   }
   // Input frame: x = J v with J = [[c,-s,0],[s,c,0],[0,0,1]].
   double x00 = fma(L.c, v[0][0], -L.s * v[0][1]), x01 = fma(L.s, v[0][0], L.c * v[0][1]), x02 = v[0][2];
