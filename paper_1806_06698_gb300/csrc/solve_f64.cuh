@@ -177,7 +177,7 @@ __device__ __forceinline__ void seed32x2(const float ab, const float b1[2], cons
 __device__ __forceinline__ int finish64(const double ab, const double b1, const double b2, const double g,
                                         const double c, const double K, const float abf, const float b2f,
                                         double& x) {
-  // x >= 2^-900 and ab, b1, b2 >= 2^-100 (checked by the caller; abf, b2f
+  // x >= 2^-900, ab >= 2^-100 and b1, b2 >= 2^-120 (checked by the caller; abf, b2f
   // are ab, b2 rounded to FP32): every quantity compared below is a normal
   // positive number or a finite f, so the comparisons run on bit patterns
   // (see arith.cuh).

@@ -179,9 +179,14 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
       const double bb1 = L.b1 * L.b1, bb2 = L.b2 * L.b2;
       pb1[0] = bb1; pb2[0] = bb2; pg[0] = L.g - L.a1;
       pb1[1] = bb2; pb2[1] = bb1; pg[1] = L.a2 - L.g;
-      // FP32 can carry the problem when its data are normal FP32 numbers.
-      const bool fp32_ok = hi_mag(bb1) >= hi_pow2(-100) && hi_mag(bb2) >= hi_pow2(-100) &&
-                           hi_mag(ab) >= hi_pow2(-100);  // all three >= 2^-100 (all >= 0)
+      // FP32 can carry the problem when its data are normal FP32 numbers
+      // with room for the products formed from them: spikes^2 >= 2^-120
+      // (a tiny spike gives a root near its own size, 1/x^2 terms up to
+      // ~2^120) and abar >= 2^-100.  An FP32 value that still underflows only
+      // makes the FP64 step more cautious or sends the root to the full
+      // iteration; acceptance is always the FP64 stopping test.
+      const bool fp32_ok = hi_mag(bb1) >= hi_pow2(-120) && hi_mag(bb2) >= hi_pow2(-120) &&
+                           hi_mag(ab) >= hi_pow2(-100);  // (all three >= 0)
       float sd[2] = {0.f, 0.f};
       double pc[2] = {0.0, 0.0}, pK[2] = {0.0, 0.0};
       const float fab = (float)ab, fb2[2] = {(float)pb2[0], (float)pb2[1]};
