@@ -41,6 +41,45 @@ FLOPS_PER_MATRIX_F64 = 313.7
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz.
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
+
+# DRAM traffic per launch: measured by ncu on one launch of each kernel
+# (--profile-case), stored per matrix in profiles/traffic.json together with
+# a hash of the sources the kernel is built from, and reported only while
+# that hash still matches (a changed kernel reports null).
+_CSRC = os.path.join(ROOT, "paper_1806_06698_gb300", "csrc")
+_COMMON = ["arith.cuh", "common.cuh", "internal.h", "../build.py"]
+TRAFFIC_CASES = {
+    # case: (kernel, sources, workload)
+    "f64": ("k_syev3_f64", ["syev3_f64.cu", "solve_f64.cuh"] + _COMMON, "mixed FP64"),
+    "f32": ("k_syev3_f32", ["syev3_f32.cu", "solve_f64.cuh"] + _COMMON, "mixed FP32, plain"),
+    "f32c": ("k_syev3_f32", ["syev3_f32.cu", "solve_f64.cuh"] + _COMMON, "mixed FP32, compensated"),
+    "bwd64": ("k_syev3_bwd", ["syev3_bwd.cu"] + _COMMON, "spectral FP64 backward"),
+    "bwd32": ("k_syev3_bwd", ["syev3_bwd.cu"] + _COMMON, "spectral FP32 backward"),
+}
+
+
+def sources_hash(case: str) -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in TRAFFIC_CASES[case][1]:
+        with open(os.path.normpath(os.path.join(_CSRC, f)), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(case: str, n: int):
+    """Measured DRAM bytes of one launch on n matrices, or None when no
+    capture matches the current sources."""
+    try:
+        with open(TRAFFIC_JSON) as fh:
+            rec = json.load(fh).get(case)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("sources") != sources_hash(case):
+        return None
+    return rec["bytes_per_matrix"] * n
 
 
 def parse():
@@ -54,6 +93,11 @@ def parse():
     p.add_argument("--fp64-only", action="store_true", help="only the FP64 headline leg")
     p.add_argument("--serve-seconds", type=float, default=10.0,
                    help="length of the Poisson serving run (the full configuration is 60)")
+    p.add_argument("--profile-case", choices=sorted(TRAFFIC_CASES),
+                   help="run exactly one launch of one kernel on its workload (for an ncu capture) and exit")
+    p.add_argument("--record-traffic", metavar="NCU_CSV",
+                   help="with --profile-case: read that case's ncu capture (dram__bytes_read.sum, "
+                        "dram__bytes_write.sum) and store its bytes per matrix in profiles/traffic.json")
     return p.parse_args()
 
 
@@ -219,7 +263,8 @@ def _fp32_legs(args, dev, stream, barrier, A64_dev):
         idx = torch.arange(0, n, max(1, n // (1 << 18)), device=dev)
         A_ref = A[idx].double().contiguous()
         lam_ref, _ = syev3.syev3_batched(A_ref, stream=stream)
-        nrm = torch.linalg.vector_norm(lam_ref, dim=1)
+        lam_ref_h = lam_ref.cpu().numpy()
+        nrm_h = np.linalg.norm(lam_ref_h, axis=1)
         for mode in ("plain", "compensated"):
             comp = mode == "compensated"
             ctr = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device=dev)
@@ -230,16 +275,18 @@ def _fp32_legs(args, dev, stream, barrier, A64_dev):
             total_ms, kms = _timed(step, args.steps, args.warmup, stream, barrier)
             syev3.syev3_batched(A, out=(lam, U), compensated=comp, counters=ctr, stream=stream)
             barrier()
-            dl = ((lam[idx].double() - lam_ref).abs().amax(dim=1) / nrm.clamp_min(1e-300)).max().item()
-            orth = torch.linalg.matrix_norm(U[idx].double().transpose(1, 2) @ U[idx].double()
-                                            - torch.eye(3, dtype=torch.float64, device=dev)).max().item()
+            # Accuracy on the host (no library GEMM in the bench's launch list).
+            lam_s, U_s = lam[idx].double().cpu().numpy(), U[idx].double().cpu().numpy()
+            dl = float(np.max(np.max(np.abs(lam_s - lam_ref_h), axis=1) / np.maximum(nrm_h, 1e-300)))
+            orth = float(np.max(np.linalg.norm(np.einsum("nki,nkj->nij", U_s, U_s) - np.eye(3), axis=(1, 2))))
             k = statistics.mean(kms)
             gbs = 72 * n / (k * 1e-3) / 1e9
             out[f"{name}_{mode}"] = {
                 "value": n * args.steps / (total_ms * 1e-3), "unit": UNIT, "ms_per_step": total_ms / args.steps,
                 "dtype": "f32", "n": n,
                 "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                             "traffic": None, "kernel": "k_syev3_f32", "peak_source": "MEASURED_PEAKS hbm_gbs"},
+                             "traffic": traffic_per_launch("f32c" if comp else "f32", n),
+                             "kernel": "k_syev3_f32", "peak_source": "MEASURED_PEAKS hbm_gbs"},
                 "fp64_refined_fraction": ctr[2].item() / n if comp else 0.0,
                 "max_dlambda_vs_fp64_kernel_eps32": dl / 2.0 ** -23,
                 "max_orthogonality_eps32": orth / 2.0 ** -23,
@@ -290,7 +337,7 @@ def _bwd_legs(args, dev, stream, barrier):
         else:
             roof = {"bound": "hbm", "achieved": BWD_BYTES[name] * rate / 1e9, "peak": hbm, "unit": "GB/s",
                     "frac": BWD_BYTES[name] * rate / 1e9 / hbm}
-        roof.update({"kernel": "k_syev3_bwd", "traffic": None})
+        roof.update({"kernel": "k_syev3_bwd", "traffic": traffic_per_launch("bwd" + name[1:], n)})
         out[f"backward_{name}_2^20"] = {"value": n * args.steps / (total_ms * 1e-3), "unit": "gradients/s",
                                         "ms_per_step": total_ms / args.steps, "n": n, "roofline": roof}
         del A, lam, U, w, V, gA
@@ -435,6 +482,7 @@ def run_native(args):
                     "kernel_ms": kms,
                     "hbm_frac_of_measured": (BYTES_PER_MATRIX_F64 * n / (kms * 1e-3) / 1e9) /
                     load_peaks().get("hbm_gbs", 6686.1)}
+        roofline["traffic"] = traffic_per_launch("f64", n)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -464,8 +512,92 @@ def run_native(args):
         torch.distributed.destroy_process_group()
 
 
+def _profile_inputs(case: str, n: int):
+    from paper_1806_06698_gb300 import inputs
+
+    if case == "f64":
+        return inputs.mixed(n, seed=inputs.SEED_BASE + 1)[0]
+    if case in ("f32", "f32c"):
+        return inputs.mixed_fp32(n)[0]
+    return inputs.spectral(n, seed=inputs.SEED_BASE + 4)[0]
+
+
+def run_profile_case(args):
+    """One launch of one kernel on its workload (n matrices): the command an
+    ncu capture of that kernel runs.  The backward cases first run the
+    forward solve they differentiate (a k_syev3_f64/f32 launch)."""
+    import torch
+
+    from paper_1806_06698_gb300 import build, syev3
+
+    build.build()
+    case, n = args.profile_case, args.n
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    dt = torch.float32 if case in ("f32", "f32c", "bwd32") else torch.float64
+    A = torch.from_numpy(_profile_inputs(case, n)).to(dev, dt)
+    lam = torch.empty((n, 3), dtype=dt, device=dev)
+    U = torch.empty((n, 3, 3), dtype=dt, device=dev)
+    syev3.syev3_batched(A, out=(lam, U), compensated=(case == "f32c"), stream=stream)
+    if case.startswith("bwd"):
+        rng = np.random.default_rng(1806066986)
+        w = torch.from_numpy(rng.standard_normal((n, 3))).to(dev, dt)
+        V = torch.from_numpy(rng.standard_normal((n, 3, 3))).to(dev, dt)
+        gA = torch.empty((n, 6), dtype=dt, device=dev)
+        syev3.syev3_batched_bwd(lam, U, w, V, 1e-6, out=gA, stream=stream)
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"profile_case": case, "n": n, "kernel": TRAFFIC_CASES[case][0]}), flush=True)
+
+
+_BYTE_UNITS = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+
+
+def record_traffic(args):
+    """Store DRAM bytes per matrix of --profile-case from its ncu CSV
+    (the first launch of the case's kernel in the capture)."""
+    import csv
+
+    case, n = args.profile_case, args.n
+    kernel = TRAFFIC_CASES[case][0]
+    with open(args.record_traffic) as fh:
+        rows = list(csv.reader(line for line in fh if line.startswith('"')))
+    hdr = rows[0]
+    ki, mi, ui, vi, ii = (hdr.index(k) for k in ("Kernel Name", "Metric Name", "Metric Unit", "Metric Value", "ID"))
+    launch, got = None, {}
+    for r in rows[1:]:
+        if kernel not in r[ki]:
+            continue
+        if launch is None:
+            launch = r[ii]
+        if r[ii] != launch:
+            break
+        if r[mi].startswith("dram__bytes_"):
+            got[r[mi]] = float(r[vi].replace(",", "")) * _BYTE_UNITS[r[ui]]
+    rd, wr = got["dram__bytes_read.sum"], got["dram__bytes_write.sum"]
+    try:
+        with open(TRAFFIC_JSON) as fh:
+            table = json.load(fh)
+    except (OSError, ValueError):
+        table = {}
+    table[case] = {"kernel": kernel, "workload": TRAFFIC_CASES[case][2], "n": n, "sources": sources_hash(case),
+                   "dram_read_bytes": rd, "dram_write_bytes": wr, "bytes_per_matrix": (rd + wr) / n,
+                   "command": f"ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                              f"--clock-control none -k regex:{kernel} -c 1 --csv "
+                              f"python bench.py --profile-case {case} --n {n}"}
+    with open(TRAFFIC_JSON, "w") as fh:
+        json.dump(table, fh, indent=1, sort_keys=True)
+        fh.write("\n")
+    print(json.dumps(table[case]))
+
+
 def main():
     args = parse()
+    if args.profile_case and args.record_traffic:
+        record_traffic(args)
+        return
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
