@@ -409,10 +409,11 @@ __device__ __forceinline__ void finish_lane(const Lane& L, double mu, double nu,
       const double inv = rsqrt(ss);
       v[k][0] *= inv; v[k][1] *= inv; v[k][2] *= inv;
     }
-    // The middle vector as u1 x u3 instead of its closed form: u1 and u3 are
-    // unit and orthogonal to rounding, so the product is unit without a
-    // normalisation, and its error is at most the sum of theirs, each within
-    // eps / gap of its eigenvalue <= eps / (gap of the middle eigenvalue).
+    // u2 is the cross product of u1 and u3 (Sec. 1.3 relies on exactly
+    // this for its orthogonality); formed here from the normalised u1 and u3,
+    // which are unit and orthogonal to rounding, so the product is unit
+    // without a normalisation, and its error is at most the sum of theirs,
+    // each within eps / gap of its eigenvalue <= eps / (middle gap).
     v[1][0] = fma(v[0][1], v[2][2], -v[0][2] * v[2][1]);
     v[1][1] = fma(v[0][2], v[2][0], -v[0][0] * v[2][2]);
     v[1][2] = fma(v[0][0], v[2][1], -v[0][1] * v[2][0]);

@@ -164,13 +164,15 @@ __device__ __forceinline__ Lane32 make_lane32(const float a_in[6]) {
 // x - Delta (Eq. (6)), or the zero of phi_j taken directly when Delta >= x/2.
 // *fx receives f(x).
 __device__ __forceinline__ float bg_step32(const float ab, const float b1, const float b2, const float g,
-                                          const float c, const float K, const float x, float* fx) {
+                                          const float c, const float K, const float x, float* fx,
+                                          float* fpx = nullptr) {
   const float r1 = rcp32(x), r2 = rcp32(x + ab);
   const float t1 = b1 * r1, t2 = b2 * r2;
   const bool small = x < ab;
   const float f = ((x + (small ? K : -g)) - t1) + (small ? c * x * r2 : -t2);
   *fx = f;
   const float fp = fmaf(t2, r2, fmaf(t1, r1, 1.f));
+  if (fpx) *fpx = fp;
   const float w0 = fmaf(t2 * ab, r2 * r2, 1.f);
   const float rb = rcp32(fmaf(f, r1, fp));
   const float fr = f * rb;
@@ -215,9 +217,9 @@ __device__ __forceinline__ void roots32(const float ab, const float b1[2], const
 __device__ bool roots32_more(const float ab, const float b1, const float b2, const float g, float* x) {
   const float c = b2 * rcp32(ab), K = -g - c;
   for (int it = 0; it < kMaxIt32; ++it) {
-    float f;
-    const float xn = bg_step32(ab, b1, b2, g, c, K, *x, &f);
-    const bool go = f > (kCTerm32 * kEps32) * (*x) && xn < *x;
+    float f, fp;
+    const float xn = bg_step32(ab, b1, b2, g, c, K, *x, &f, &fp);
+    const bool go = f > (kCTerm32 * kEps32) * (*x) * fp && xn < *x;  // f/f' >= C eps x: not yet
     *x = xn;
     if (!go) return true;
   }
