@@ -344,6 +344,128 @@ def _bwd_legs(args, dev, stream, barrier):
     return out
 
 
+def _host_errors(A6: np.ndarray, lam: np.ndarray, U: np.ndarray):
+    """Per matrix, on the host in FP64: ||A U - U Lambda||_F / ||A||_F and
+    ||U^T U - I||_F."""
+    from paper_1806_06698_gb300 import inputs
+
+    M = inputs.unpack(A6)
+    nrm = np.linalg.norm(M, axis=(1, 2))
+    res = np.linalg.norm(M @ U - U * lam[:, None, :], axis=(1, 2)) / np.where(nrm > 0, nrm, 1.0)
+    orth = np.linalg.norm(np.einsum("nki,nkj->nij", U, U) - np.eye(3), axis=(1, 2))
+    return res, orth
+
+
+def _method_study_leg(args, dev, stream, barrier):
+    """The method variants (syev3_batched_method) on the mixed batch and its
+    subsets: the production path, the FP64 Borges-Gragg iteration from
+    Eq. (7) and Newton's method (Sec. 1.4.2); then the simplified against the
+    EISPACK-style deflation test (Sec. 1.1)."""
+    import torch
+
+    from paper_1806_06698_gb300 import inputs, syev3
+
+    n = max(1 << 12, args.n // 4)
+    A_np, ids = inputs.mixed(n, seed=inputs.SEED_BASE + 1)
+    names = {"production": syev3.ZF_PRODUCTION, "borges_gragg": syev3.ZF_BORGES_GRAGG, "newton": syev3.ZF_NEWTON}
+    subsets = [("mixed", None)] + [(v, k) for k, v in inputs.SUBSET_NAMES.items()]
+    sample = 1 << 14
+    out = {"n": n, "zero_finder": {}, "deflation_test": {}}
+    for sub, sid in subsets:
+        Ah = A_np if sid is None else np.ascontiguousarray(A_np[ids == sid])
+        m = Ah.shape[0]
+        A = torch.from_numpy(Ah).to(dev)
+        lam = torch.empty((m, 3), dtype=torch.float64, device=dev)
+        U = torch.empty((m, 3, 3), dtype=torch.float64, device=dev)
+        idx = np.linspace(0, m - 1, min(m, sample)).astype(np.int64)
+        lam_bg = None
+        rows = {}
+        for name in ("borges_gragg", "production", "newton"):
+            zf = names[name]
+            stats = torch.zeros(len(syev3.METHOD_STATS), dtype=torch.int64, device=dev)
+
+            def step():
+                syev3.syev3_batched_method(A, zero_finder=zf, out=(lam, U), stream=stream)
+
+            total_ms, _ = _timed(step, args.steps if args.steps < 10 else 10, 2, stream, barrier)
+            reps = args.steps if args.steps < 10 else 10
+            syev3.syev3_batched_method(A, zero_finder=zf, out=(lam, U), stats=stats, stream=stream)
+            barrier()
+            st = dict(zip(syev3.METHOD_STATS, stats.cpu().tolist()))
+            lam_s, U_s = lam.cpu().numpy()[idx], U.cpu().numpy()[idx]
+            res, orth = _host_errors(Ah[idx], lam_s, U_s)
+            nrm = np.linalg.norm(inputs.unpack(Ah[idx]), axis=(1, 2))
+            row = {"value": m * reps / (total_ms * 1e-3), "unit": UNIT,
+                   "steps_per_root": st["steps"] / max(1, st["roots"]),
+                   "simt_efficiency": st["steps"] / max(1, st["warp_slots"]),
+                   "roots_full_iteration": st["roots"], "capped": st["capped"],
+                   "max_residual_rel": float(res.max()), "max_orthogonality": float(orth.max())}
+            if lam_bg is None:
+                lam_bg = lam_s
+            else:
+                row["max_dlambda_vs_borges_gragg_rel"] = float(
+                    np.max(np.max(np.abs(lam_s - lam_bg), axis=1) / np.where(nrm > 0, nrm, 1.0)))
+            rows[name] = row
+        out["zero_finder"][sub] = rows
+        del A, lam, U
+    # Deflation test: simplified (Sec. 1.1, adopted) vs EISPACK-style.
+    for name, Ah in (("mixed", A_np), ("trace_free_spiked", inputs.trace_free_spiked(min(n, 1 << 20)))):
+        m = Ah.shape[0]
+        A = torch.from_numpy(Ah).to(dev)
+        res_l = {}
+        row = {}
+        for defl, key in ((syev3.DEFLATION_SIMPLIFIED, "simplified"), (syev3.DEFLATION_EISPACK, "eispack")):
+            stats = torch.zeros(len(syev3.METHOD_STATS), dtype=torch.int64, device=dev)
+            lam, U = syev3.syev3_batched_method(A, deflation_test=defl, stats=stats, stream=stream)
+            barrier()
+            st = dict(zip(syev3.METHOD_STATS, stats.cpu().tolist()))
+            idx = np.linspace(0, m - 1, min(m, sample)).astype(np.int64)
+            res, orth = _host_errors(Ah[idx], lam.cpu().numpy()[idx], U.cpu().numpy()[idx])
+            res_l[key] = lam.cpu().numpy()
+            row[key] = {"deflated_fraction": st["deflated"] / m, "max_residual_rel": float(res.max()),
+                        "max_orthogonality": float(orth.max())}
+        nrm = np.linalg.norm(inputs.unpack(Ah), axis=(1, 2))
+        row["max_dlambda_between_rel"] = float(np.max(np.max(np.abs(res_l["eispack"] - res_l["simplified"]), axis=1)
+                                                     / np.where(nrm > 0, nrm, 1.0)))
+        out["deflation_test"][name] = row
+        del A
+    torch.cuda.empty_cache()
+    return out
+
+
+def _accuracy_experiment(dev, stream, n: int = 100_000):
+    """The test of Sec. 1.5 on this solver: n symmetric matrices with iid
+    entries from U(0,1), N(0,1) and chi^2_1; ||I - V^T V||_F and
+    ||T V - V Lambda||_F of the FP64 kernel and of LAPACK (numpy.linalg.eigh),
+    differenced per matrix as LAPACK minus ours (positive where ours is more
+    accurate) and summarised (the paper plots them sorted)."""
+    import torch
+
+    from paper_1806_06698_gb300 import inputs, syev3
+
+    out = {"n": n, "reference": "numpy.linalg.eigh (LAPACK dsyevd) on the host"}
+    for dist in ("uniform", "normal", "chisq"):
+        T6 = inputs.paper_set(n, dist)
+        lam, U = syev3.syev3_batched(torch.from_numpy(T6).to(dev), stream=stream)
+        torch.cuda.synchronize(dev)
+        lam, U = lam.cpu().numpy(), U.cpu().numpy()
+        M = inputs.unpack(T6)
+        lam_l, U_l = np.linalg.eigh(M)
+        row = {}
+        for meas, f in (("orthogonality", lambda L, V: np.linalg.norm(np.einsum("nki,nkj->nij", V, V) - np.eye(3),
+                                                                         axis=(1, 2))),
+                        ("residual", lambda L, V: np.linalg.norm(M @ V - V * L[:, None, :], axis=(1, 2)))):
+            ours, ref = f(lam, U), f(lam_l, U_l)
+            d = np.sort(ref - ours)
+            row[meas] = {"ours_median": float(np.median(ours)), "lapack_median": float(np.median(ref)),
+                         "ours_max": float(ours.max()), "lapack_max": float(ref.max()),
+                         "frac_ours_better": float(np.mean(d > 0)), "frac_equal": float(np.mean(d == 0)),
+                         "frac_lapack_better": float(np.mean(d < 0)),
+                         "diff_quantiles_1_50_99": [float(np.quantile(d, q)) for q in (0.01, 0.5, 0.99)]}
+        out[dist] = row
+    return out
+
+
 def _serving_leg(args, dev, A64):
     """Serving form: Poisson arrivals at 2000 requests/s for --serve-seconds,
     each request N = floor(exp(U(0, ln 2^22))) matrices, 70 % FP64 / 30 %
@@ -472,6 +594,8 @@ def run_native(args):
     fp32 = None if args.fp64_only else _fp32_legs(args, dev, stream, barrier, A)
     bwd = None if args.fp64_only else _bwd_legs(args, dev, stream, barrier)
     serving = None if (args.fp64_only or args.serve_seconds <= 0) else _serving_leg(args, dev, A)
+    study = None if args.fp64_only else _method_study_leg(args, dev, stream, barrier)
+    accuracy = None if args.fp64_only else _accuracy_experiment(dev, stream)
 
     if rank == 0:
         kms = statistics.mean(kernel_ms)
@@ -505,6 +629,10 @@ def run_native(args):
             line["differentiation_form"] = bwd
         if serving is not None:
             line["serving"] = serving
+        if study is not None:
+            line["method_study"] = study
+        if accuracy is not None:
+            line["accuracy_experiment"] = accuracy
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(A_np, n)
         print(json.dumps(line), flush=True)

@@ -94,6 +94,53 @@ int syev3_batched(const void* A_packed6, int64_t n, void* lambda, void* U, int d
 int syev3_batched_ex(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype,
                      uint64_t* d_counters, syev3_stream_t stream);
 
+/* syev3_batched_method -- syev3_batched (FP64 only) with the variants of
+ * the method the paper also describes, for studying them against the
+ * production path:
+ *   zero_finder    : SYEV3_ZF_PRODUCTION -- the path of syev3_batched (FP32
+ *                    Borges-Gragg seeds, one FP64 step and the stopping test);
+ *                    SYEV3_ZF_BORGES_GRAGG -- the Borges-Gragg iteration of
+ *                    Sec. 1.4.1 in FP64 from the start of Eq. (7);
+ *                    SYEV3_ZF_NEWTON -- Newton's method of Sec. 1.4.2 in FP64,
+ *                    started left of the zero, stopped when |f| < 2 eps x.
+ *   deflation_test : SYEV3_DEFLATION_SIMPLIFIED -- the test the paper adopts,
+ *                    |abar b1 b2| <= eps |a1 + a2| h^2 (Sec. 1.1);
+ *                    SYEV3_DEFLATION_EISPACK -- the EISPACK-style test it is
+ *                    derived from, |abar b1 b2| <= eps (|a1 b2^2 + a2 b1^2| +
+ *                    |a1 b1^2 + a2 b2^2|).
+ *   d_stats        : device, SYEV3_METHOD_STATS x uint64, or NULL; the
+ *                    kernel adds [0] lanes whose zero finder hit the 64-step
+ *                    cap, [1] non-finite lanes, [2] diagonal, [3] deflated and
+ *                    [4] reduced arrows, [5] zero-finder steps taken by the
+ *                    full FP64 iteration, [6] roots it solved, [7] the FP64
+ *                    lane-slots its warps spent (32 x the longest iteration of
+ *                    each warp; [5]/[7] is the iteration's SIMT efficiency).
+ *                    With SYEV3_ZF_PRODUCTION, [5]-[7] cover only the roots the
+ *                    seeded step leaves to the full iteration.  The caller
+ *                    zeroes them; they accumulate.
+ * Arguments and errors otherwise as syev3_batched; SYEV3_EINVAL also for a
+ * dtype other than SYEV3_F64, a NULL method or an unknown variant. */
+typedef enum {
+  SYEV3_ZF_PRODUCTION = 0,
+  SYEV3_ZF_BORGES_GRAGG = 1,
+  SYEV3_ZF_NEWTON = 2
+} syev3_zero_finder;
+
+typedef enum {
+  SYEV3_DEFLATION_SIMPLIFIED = 0,
+  SYEV3_DEFLATION_EISPACK = 1
+} syev3_deflation_test;
+
+#define SYEV3_METHOD_STATS 8
+
+typedef struct {
+  int zero_finder;    /* a syev3_zero_finder */
+  int deflation_test; /* a syev3_deflation_test */
+} syev3_method;
+
+int syev3_batched_method(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype,
+                         const syev3_method* method, uint64_t* d_stats, syev3_stream_t stream);
+
 /* syev3_batched_bwd -- gradient of a loss through syev3_batched, packed.
  * Not in the paper: the standard derivative of simple eigenpairs,
  *   Abar = U (diag(g_lambda) + F o (U^T g_U)) U^T,

@@ -13,6 +13,21 @@ constexpr int kNumCounters = 4;
 cudaError_t launch_f64(const double* A, int64_t n, double* lam, double* U, unsigned long long* counters,
                        cudaStream_t stream);
 
+// Method study (syev3_batched_method): values match syev3_zero_finder and
+// syev3_deflation_test of syev3.h.
+constexpr int kZfProduction = 0, kZfBorgesGragg = 1, kZfNewton = 2;
+constexpr int kDeflSimplified = 0, kDeflEispack = 1;
+struct Method {
+  int zero_finder;
+  int deflation_test;
+};
+// Statistics layout of syev3_batched_method (8 words).
+constexpr int kStatCapped = 0, kStatNonFinite = 1, kStatDiagonal = 2, kStatDeflated = 3, kStatReduced = 4,
+              kStatSteps = 5, kStatRoots = 6, kStatWarpSlots = 7, kNumStats = 8;
+
+cudaError_t launch_f64_method(const double* A, int64_t n, double* lam, double* U, unsigned long long* stats,
+                              Method method, cudaStream_t stream);
+
 cudaError_t launch_f32(const float* A, int64_t n, float* lam, float* U, bool compensated,
                        unsigned long long* counters, cudaStream_t stream);
 

@@ -240,7 +240,7 @@ __device__ __forceinline__ double newton64(const double ab, const double b1, con
 // right of the root, or from the start of Eq. (7) when x0 <= 0.  The next
 // iterate is x - Delta (Eq. (6)), or the zero of phi_j taken directly when
 // Delta >= x/2.
-__device__ double zero_bg_full(double ab, double b1, double b2, double g, double x, bool& capped) {
+__device__ double zero_bg_full(double ab, double b1, double b2, double g, double x, bool& capped, int& steps) {
   if (!(x > 0.0)) {
     const double hg = 0.5 * g, bs = b1 + b2;
     const double rt = sqrt(fma(hg, hg, bs));
@@ -248,7 +248,8 @@ __device__ double zero_bg_full(double ab, double b1, double b2, double g, double
   }
   const double c = b2 / ab, K = -g - c;  // f = x + K - b1/x + c x/(x + ab)
   capped = false;
-  for (int it = 0;; ++it) {
+  int it = 0;
+  for (;; ++it) {
     const double r1 = 1.0 / x, r2 = 1.0 / (x + ab);
     const double t1 = b1 * r1, t2 = b2 * r2;
     const bool small = x < ab;
@@ -280,6 +281,37 @@ __device__ double zero_bg_full(double ab, double b1, double b2, double g, double
     if (!(xn < x)) break;
     x = xn;
   }
+  steps = it;
+  return x;
+}
+
+// Newton's method of Sec. 1.4.2 in FP64 (IEEE arithmetic, printed form of
+// f): started left of the zero at the positive zero of x - g - b1/x (the
+// point where f meets -b2/(x + ab); conjugate form when g < 0), stopped when
+// |f| < C eps x, when f >= 0 (at or past the zero: rounding level, the
+// iteration being monotone from the left) or when a step no longer
+// increases x.  Sets steps and capped (kMaxIt steps without a stop).
+__device__ double zero_newton_full(double ab, double b1, double b2, double g, bool& capped, int& steps) {
+  const double hg = 0.5 * g;
+  const double rt = sqrt(fma(hg, hg, b1));
+  double x = (g >= 0.0) ? hg + rt : b1 / (rt - hg);
+  capped = false;
+  int it = 0;
+  for (;; ++it) {
+    const double r1 = 1.0 / x, r2 = 1.0 / (x + ab);
+    const double f = ((x - g) - b1 * r1) - b2 * r2;
+    const double fp = fma(b2 * r2, r2, fma(b1 * r1, r1, 1.0));
+    if (!(f < 0.0)) break;
+    if (-f < (kCTerm * kEps) * x) break;
+    if (it >= kMaxIt) {
+      capped = true;
+      break;
+    }
+    const double xn = x - f / fp;
+    if (!(xn > x)) break;
+    x = xn;
+  }
+  steps = it;
   return x;
 }
 
@@ -294,6 +326,9 @@ struct Lane {
 };
 
 // Phase A: pre-scale, Sec. 1 arrow reduction, Sec. 1.1 classification.
+// kEispack selects the EISPACK-style deflation test of Sec. 1.1 (the form
+// the paper starts from) instead of the simplified one it adopts.
+template <bool kEispack = false>
 __device__ __forceinline__ Lane make_lane(const double a_in[6]) {
   Lane L;
   int E = 0;
@@ -350,9 +385,14 @@ __device__ __forceinline__ Lane make_lane(const double a_in[6]) {
   const double abar = L.a1 - L.a2;
   const double h2 = fma(b1, b1, b2 * b2);
   // Both sides of the deflation test are >= +0: compared as bit patterns.
+  // Simplified: |abar b1 b2| <= C eps |a1 + a2| h^2; EISPACK-style:
+  // |abar b1 b2| <= C eps (|a1 b2^2 + a2 b1^2| + |a1 b1^2 + a2 b2^2|).
+  const double rhs = kEispack ? (kCDefl * kEps) * (fabs(fma(L.a1 * b2, b2, L.a2 * b1 * b1)) +
+                                                    fabs(fma(L.a1 * b1, b1, L.a2 * b2 * b2)))
+                              : (kCDefl * kEps) * fabs(L.a1 + L.a2) * h2;
   if (dbits(h2) == 0)
     L.cls = kDiagonal;
-  else if (dbits(fabs(abar * b1 * b2)) <= dbits((kCDefl * kEps) * fabs(L.a1 + L.a2) * h2))
+  else if (dbits(fabs(abar * b1 * b2)) <= dbits(rhs))
     L.cls = kDeflated;  // also the exact beta- and combo-deflations
   else
     L.cls = kReduced;

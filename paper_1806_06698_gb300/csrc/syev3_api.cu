@@ -103,6 +103,26 @@ int syev3_batched(const void* A_packed6, int64_t n, void* lambda, void* U, int d
   return syev3_batched_ex(A_packed6, n, lambda, U, dtype, nullptr, stream);
 }
 
+int syev3_batched_method(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype,
+                         const syev3_method* method, uint64_t* d_stats, syev3_stream_t stream) {
+  if (dtype != SYEV3_F64 || method == nullptr) return SYEV3_EINVAL;
+  if (method->zero_finder < SYEV3_ZF_PRODUCTION || method->zero_finder > SYEV3_ZF_NEWTON) return SYEV3_EINVAL;
+  if (method->deflation_test != SYEV3_DEFLATION_SIMPLIFIED && method->deflation_test != SYEV3_DEFLATION_EISPACK)
+    return SYEV3_EINVAL;
+  const int st = check_forward(A_packed6, n, lambda, U, dtype);
+  if (st != SYEV3_OK || n == 0) return st;
+  if (d_stats && (!aligned(d_stats, 8) || !device_accessible(d_stats))) return SYEV3_EINVAL;
+  static_assert(SYEV3_ZF_NEWTON == syev3::kZfNewton && SYEV3_ZF_BORGES_GRAGG == syev3::kZfBorgesGragg &&
+                    SYEV3_DEFLATION_EISPACK == syev3::kDeflEispack && SYEV3_METHOD_STATS == syev3::kNumStats,
+                "syev3.h and internal.h disagree");
+  const syev3::Method m{method->zero_finder, method->deflation_test};
+  const cudaError_t e = syev3::launch_f64_method(static_cast<const double*>(A_packed6), n,
+                                                 static_cast<double*>(lambda), static_cast<double*>(U),
+                                                 reinterpret_cast<unsigned long long*>(d_stats), m,
+                                                 reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SYEV3_OK : cuda_fail(e);
+}
+
 int syev3_batched_bwd(const void* lambda, const void* U, const void* g_lambda, const void* g_U, int64_t n,
                       void* g_A_packed6, double gap_tau, int dtype, syev3_stream_t stream) {
   if (!valid_dtype(dtype) || n < 0 || !(gap_tau >= 0.0) || gap_tau > 1e300) return SYEV3_EINVAL;

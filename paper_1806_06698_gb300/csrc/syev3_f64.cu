@@ -39,10 +39,17 @@ __device__ unsigned g_flags;     // kFlagWaitTimeout when a bulk-copy wait ran o
 // The kernel
 // ---------------------------------------------------------------------------
 
-template <bool kBulkIn>
+// kStudy: the method-study build (syev3_batched_method).  The zero finder
+// and the deflation test are then chosen at run time by `method`, and
+// `counters` receives the 8 method statistics (MethodStat) instead of the
+// 4 counters of syev3_batched_ex.  The production build (kStudy = false)
+// has these switches compiled out.
+template <bool kBulkIn, bool kStudy>
 __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A, int64_t n,
                                                     double* __restrict__ lam_out, double* __restrict__ U_out,
-                                                    unsigned long long* __restrict__ counters) {
+                                                    unsigned long long* __restrict__ counters, Method method) {
+  const int zf = kStudy ? method.zero_finder : kZfProduction;
+  const bool eispack = kStudy && method.deflation_test == kDeflEispack;
   __shared__ alignas(16) double s_in[2][kTPB * 6];
   __shared__ alignas(16) double s_lam[kTPB * 3];
   __shared__ alignas(16) double s_U[kTPB * 9];
@@ -120,7 +127,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
         const double2* src = reinterpret_cast<const double2*>(&s_in[buf][tid * 6]);
         const double2 p0 = src[0], p1 = src[1], p2 = src[2];
         const double a[6] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y};
-        A0 = make_lane(a);
+        A0 = eispack ? make_lane<true>(a) : make_lane<false>(a);
       }
       // Reorder by class: reduced arrows take slots 0, 1, ... and the other
       // classes slots cnt-1, cnt-2, ..., so that the warps below run either
@@ -174,7 +181,14 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
     double root[2] = {0.0, 0.0};
     bool hard[2] = {false, false};
     double ab = 0.0, pb1[2] = {0.0, 0.0}, pb2[2] = {0.0, 0.0}, pg[2] = {0.0, 0.0};
-    if (reduced) {
+    if (reduced && zf != kZfProduction) {
+      // Study: every root goes to the full FP64 iteration from the paper's
+      // own start (Eq. (7) for Borges-Gragg, Sec. 1.4.2 for Newton).
+      ab = L.a1 - L.a2;
+      pb1[0] = L.b1 * L.b1; pb2[0] = L.b2 * L.b2; pg[0] = L.g - L.a1;
+      pb1[1] = pb2[0]; pb2[1] = pb1[0]; pg[1] = L.a2 - L.g;
+      hard[0] = hard[1] = true;
+    } else if (reduced) {
       ab = L.a1 - L.a2;
       const double bb1 = L.b1 * L.b1, bb2 = L.b2 * L.b2;
       pb1[0] = bb1; pb2[0] = bb2; pg[0] = L.g - L.a1;
@@ -241,8 +255,25 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
     const int n_hard = s_nhard;
     for (int i = tid; i < n_hard; i += kTPB) {
       bool cp;
-      s_hx[i] = zero_bg_full(s_hab[i], s_hb1[i], s_hb2[i], s_hg[i], s_hx[i], cp);
+      int steps;
+      if (zf == kZfNewton)
+        s_hx[i] = zero_newton_full(s_hab[i], s_hb1[i], s_hb2[i], s_hg[i], cp, steps);
+      else
+        s_hx[i] = zero_bg_full(s_hab[i], s_hb1[i], s_hb2[i], s_hg[i], s_hx[i], cp, steps);
       s_hcap[i] = cp;
+      if (kStudy && counters != nullptr) {
+        // Steps, and the lane-slots the warp spent on them: on the FP64 pipe
+        // an instruction occupies all 32 lanes, so a warp costs 32 x its
+        // longest iteration.
+        const unsigned am = __activemask();
+        const unsigned sum = __reduce_add_sync(am, (unsigned)steps);
+        const unsigned mx = __reduce_max_sync(am, (unsigned)steps);
+        if ((tid & 31) == __ffs(am) - 1) {
+          atomicAdd(&counters[kStatSteps], (unsigned long long)sum);
+          atomicAdd(&counters[kStatRoots], (unsigned long long)__popc(am));
+          atomicAdd(&counters[kStatWarpSlots], 32ull * mx);
+        }
+      }
     }
     __syncthreads();
     bool capped = false;
@@ -279,6 +310,16 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
       if (lane_id == 0) {
         if (cm) atomicAdd(&counters[0], (unsigned long long)__popc(cm));
         if (nf) atomicAdd(&counters[1], (unsigned long long)__popc(nf));
+      }
+      if (kStudy) {
+        const unsigned md = __ballot_sync(0xffffffffu, L.cls == kDiagonal);
+        const unsigned mf = __ballot_sync(0xffffffffu, L.cls == kDeflated);
+        const unsigned mr = __ballot_sync(0xffffffffu, L.cls == kReduced);
+        if (lane_id == 0) {
+          if (md) atomicAdd(&counters[kStatDiagonal], (unsigned long long)__popc(md));
+          if (mf) atomicAdd(&counters[kStatDeflated], (unsigned long long)__popc(mf));
+          if (mr) atomicAdd(&counters[kStatReduced], (unsigned long long)__popc(mr));
+        }
       }
     }
     __syncthreads();
@@ -317,16 +358,30 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
   }
 }
 
-int blocks_per_sm_f64(bool bulk) {
-  static int cached[2] = {-1, -1};
-  int& c = cached[bulk ? 1 : 0];
-  if (c < 0) {
+template <bool kBulkIn, bool kStudy>
+int blocks_per_sm_f64() {
+  static int cached = -1;
+  if (cached < 0) {
     int v = 0;
-    cudaError_t e = bulk ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_syev3_f64<true>, kTPB, 0)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_syev3_f64<false>, kTPB, 0);
-    c = (e == cudaSuccess && v > 0) ? v : 1;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_syev3_f64<kBulkIn, kStudy>, kTPB, 0);
+    cached = (e == cudaSuccess && v > 0) ? v : 1;
   }
-  return c;
+  return cached;
+}
+
+template <bool kBulkIn, bool kStudy>
+cudaError_t launch_f64_t(const double* A, int64_t n, double* lam, double* U, unsigned long long* counters,
+                         Method method, cudaStream_t stream) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int64_t n_tiles = (n + kTPB - 1) / kTPB;
+  const int64_t resident = (int64_t)sms * blocks_per_sm_f64<kBulkIn, kStudy>();
+  const int grid = (int)(n_tiles < resident ? n_tiles : resident);
+  k_syev3_f64<kBulkIn, kStudy><<<grid, kTPB, 0, stream>>>(A, n, lam, U, counters, method);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -334,20 +389,17 @@ int blocks_per_sm_f64(bool bulk) {
 cudaError_t launch_f64(const double* A, int64_t n, double* lam, double* U, unsigned long long* counters,
                        cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
-  const bool bulk = (reinterpret_cast<uintptr_t>(A) & 15) == 0;
-  const int64_t n_tiles = (n + kTPB - 1) / kTPB;
-  const int64_t resident = (int64_t)sms * blocks_per_sm_f64(bulk);
-  const int grid = (int)(n_tiles < resident ? n_tiles : resident);
-  if (bulk)
-    k_syev3_f64<true><<<grid, kTPB, 0, stream>>>(A, n, lam, U, counters);
-  else
-    k_syev3_f64<false><<<grid, kTPB, 0, stream>>>(A, n, lam, U, counters);
-  return cudaGetLastError();
+  const Method m{kZfProduction, kDeflSimplified};
+  if ((reinterpret_cast<uintptr_t>(A) & 15) == 0) return launch_f64_t<true, false>(A, n, lam, U, counters, m, stream);
+  return launch_f64_t<false, false>(A, n, lam, U, counters, m, stream);
+}
+
+cudaError_t launch_f64_method(const double* A, int64_t n, double* lam, double* U, unsigned long long* stats,
+                              Method method, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  if ((reinterpret_cast<uintptr_t>(A) & 15) == 0)
+    return launch_f64_t<true, true>(A, n, lam, U, stats, method, stream);
+  return launch_f64_t<false, true>(A, n, lam, U, stats, method, stream);
 }
 
 cudaError_t take_flags_f64(unsigned* flags) {

@@ -200,3 +200,28 @@ def paper_set(n: int, dist: str, seed: int = SEED_BASE + 5) -> np.ndarray:
     if dist == "chisq":
         return rng.chisquare(1.0, (n, 6))
     raise ValueError(f"unknown distribution {dist!r}")
+
+
+def trace_free_spiked(n: int, seed: int = SEED_BASE + 7) -> np.ndarray:
+    """Matrices whose leading 2x2 block has zero trace (alpha1 + alpha2 = 0:
+    the rotation maps the pair (p, -p) to (l, -l) exactly) and whose spikes
+    differ by 10^k in size, k ~ U(4, 20):
+    the case where the simplified deflation test of Sec. 1.1 (right side
+    ~ |alpha1 + alpha2|) and the EISPACK-style test it comes from disagree.
+    Block diag(t, -t), t ~ U(0.5, 2), rotated by a uniform angle in the
+    (1,2)-plane; spikes (10^-k z1, z2) rotated with it; a33 ~ N(0,1)."""
+    rng = np.random.default_rng(seed)
+    t = rng.uniform(0.5, 2.0, n)
+    th = rng.uniform(0.0, np.pi, n)
+    k = rng.uniform(4.0, 20.0, n)
+    z1 = rng.standard_normal(n) * 10.0 ** (-k)
+    z2 = rng.standard_normal(n)
+    c, s = np.cos(th), np.sin(th)
+    A = np.empty((n, 6))
+    A[:, 0] = t * (c * c - s * s)   # R diag(t, -t) R^T
+    A[:, 1] = -A[:, 0]
+    A[:, 3] = 2.0 * t * c * s
+    A[:, 4] = c * z1 - s * z2       # R (z1, z2)
+    A[:, 5] = s * z1 + c * z2
+    A[:, 2] = rng.standard_normal(n)
+    return A

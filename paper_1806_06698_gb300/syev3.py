@@ -20,6 +20,11 @@ LIB_PATH = os.path.join(_HERE, "libsyev3.so")
 SYEV3_F64, SYEV3_F32, SYEV3_F32_COMPENSATED = 0, 1, 2
 SYEV3_OK, SYEV3_EINVAL, SYEV3_ECUDA, SYEV3_ENOCONV, SYEV3_ETIMEOUT = 0, 1, 2, 3, 4
 NUM_COUNTERS = 4
+# syev3_batched_method: variants of the zero finder and the deflation test,
+# and the layout of its statistics (include/syev3.h).
+ZF_PRODUCTION, ZF_BORGES_GRAGG, ZF_NEWTON = 0, 1, 2
+DEFLATION_SIMPLIFIED, DEFLATION_EISPACK = 0, 1
+METHOD_STATS = ("capped", "nonfinite", "diagonal", "deflated", "reduced", "steps", "roots", "warp_slots")
 
 _lock = threading.Lock()
 _lib = None
@@ -52,6 +57,8 @@ def _load():
             lib.syev3_batched.restype = i32
             lib.syev3_batched_ex.argtypes = [vp, i64, vp, vp, i32, vp, vp]
             lib.syev3_batched_ex.restype = i32
+            lib.syev3_batched_method.argtypes = [vp, i64, vp, vp, i32, ctypes.POINTER(_Method), vp, vp]
+            lib.syev3_batched_method.restype = i32
             lib.syev3_batched_bwd.argtypes = [vp, vp, vp, vp, i64, vp, ctypes.c_double, i32, vp]
             lib.syev3_batched_bwd.restype = i32
             lib.syev3_batched_host.argtypes = [vp, i64, vp, vp, i32, i64, vp]
@@ -115,6 +122,34 @@ def syev3_batched(A6: torch.Tensor, *, vectors: bool = True, compensated: bool =
     else:
         st = lib.syev3_batched_ex(_ptr(A6), n, _ptr(lam), _ptr(U), code, _ptr(counters), _stream(stream))
     _check(st, "syev3_batched")
+    return lam, U
+
+
+class _Method(ctypes.Structure):
+    _fields_ = [("zero_finder", ctypes.c_int), ("deflation_test", ctypes.c_int)]
+
+
+def syev3_batched_method(A6: torch.Tensor, *, zero_finder: int = ZF_PRODUCTION,
+                         deflation_test: int = DEFLATION_SIMPLIFIED, vectors: bool = True,
+                         out: tuple[torch.Tensor, torch.Tensor | None] | None = None,
+                         stats: torch.Tensor | None = None, stream=None):
+    """FP64 solve with a chosen zero finder and deflation test (the method
+    study entry point).  ``stats`` is an optional int64 device tensor of
+    len(METHOD_STATS) entries the kernel adds to."""
+    if not A6.is_cuda or A6.dtype != torch.float64:
+        raise ValueError("A6 must be a float64 CUDA tensor (no CPU fallback)")
+    if A6.dim() != 2 or A6.shape[1] != 6 or not A6.is_contiguous():
+        raise ValueError("A6 must be a contiguous (n, 6) tensor")
+    n = A6.shape[0]
+    if out is None:
+        lam = torch.empty((n, 3), dtype=A6.dtype, device=A6.device)
+        U = torch.empty((n, 3, 3), dtype=A6.dtype, device=A6.device) if vectors else None
+    else:
+        lam, U = out
+    m = _Method(int(zero_finder), int(deflation_test))
+    st = _load().syev3_batched_method(_ptr(A6), n, _ptr(lam), _ptr(U), SYEV3_F64, ctypes.byref(m), _ptr(stats),
+                                      _stream(stream))
+    _check(st, "syev3_batched_method")
     return lam, U
 
 

@@ -65,3 +65,23 @@ def test_host_side_argument_checks(lib):
     # n == 0 is a no-op
     assert lib.syev3_batched(None, 0, None, None, 0, None) == syev3.SYEV3_OK
     assert lib.syev3_status_string(syev3.SYEV3_EINVAL).startswith(b"SYEV3_EINVAL")
+
+
+def test_method_entry_point_argument_checks(lib):
+    from paper_1806_06698_gb300 import syev3
+
+    vp = ctypes.c_void_p
+    dummy = vp(4096)
+    ok = syev3._Method(syev3.ZF_NEWTON, syev3.DEFLATION_EISPACK)
+    call = lib.syev3_batched_method
+    # FP64 only; a method must be given and name known variants
+    assert call(dummy, 4, vp(8192), None, syev3.SYEV3_F32, ctypes.byref(ok), None, None) == syev3.SYEV3_EINVAL
+    assert call(dummy, 4, vp(8192), None, syev3.SYEV3_F64, None, None, None) == syev3.SYEV3_EINVAL
+    bad_zf = syev3._Method(3, syev3.DEFLATION_SIMPLIFIED)
+    bad_defl = syev3._Method(syev3.ZF_PRODUCTION, 2)
+    assert call(dummy, 4, vp(8192), None, syev3.SYEV3_F64, ctypes.byref(bad_zf), None, None) == syev3.SYEV3_EINVAL
+    assert call(dummy, 4, vp(8192), None, syev3.SYEV3_F64, ctypes.byref(bad_defl), None, None) == syev3.SYEV3_EINVAL
+    # the forward checks apply as for syev3_batched; n == 0 is a no-op
+    assert call(dummy, -1, vp(8192), None, syev3.SYEV3_F64, ctypes.byref(ok), None, None) == syev3.SYEV3_EINVAL
+    assert call(None, 0, None, None, syev3.SYEV3_F64, ctypes.byref(ok), None, None) == syev3.SYEV3_OK
+    assert len(syev3.METHOD_STATS) == 8
