@@ -108,6 +108,33 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device="cpu") -> float:
+    """The largest of every rank's x (all-reduce MAX); x itself when the
+    process group is not initialised (one process)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_batch(n: int, rank: int) -> np.ndarray:
+    """The batch rank `rank` solves: its own seeded 2^24 mixed batch (replicas,
+    no exchange between ranks); rank 0's is the N=1 batch."""
+    from paper_1806_06698_gb300 import inputs
+
+    return inputs.mixed(n, seed=inputs.SEED_BASE + 1 + rank)[0]
+
+
+def whole_job_rate(units_per_rank: int, world_size: int, steps: int, max_ms: float) -> float:
+    """Units of all ranks per second over the slowest rank's time (weak
+    scaling: every rank processes units_per_rank per step)."""
+    return world_size * units_per_rank * steps / (max_ms * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled every 200 ms while active."""
 
@@ -547,7 +574,7 @@ def run_native(args):
     torch.cuda.set_device(dev)
     build.build()
     n = args.n
-    A_np, _ = inputs.mixed(n, seed=inputs.SEED_BASE + 1 + rank)
+    A_np = replica_batch(n, rank)
     A = torch.from_numpy(A_np).to(dev)
     lam = torch.empty((n, 3), dtype=torch.float64, device=dev)
     U = torch.empty((n, 3, 3), dtype=torch.float64, device=dev)
@@ -565,12 +592,9 @@ def run_native(args):
     sampler.start()
     total_ms, kernel_ms = _timed(step, args.steps, args.warmup, stream, barrier)
     clocks = sampler.stop()
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dev)
     ms_per_step = total_ms / args.steps
-    value = ws * n * args.steps / (total_ms * 1e-3)
+    value = whole_job_rate(n, ws, args.steps, total_ms)
 
     # End to end through the C ABI's host entry point: pinned host buffers in,
     # the pipelined H2D copy / solve / D2H copy of eigenvalues and
@@ -585,11 +609,8 @@ def run_native(args):
         syev3.syev3_batched_host(A_host, lam_host, U_host, stream=stream)
 
     e2e_ms, _ = _timed(e2e_step, e2e_steps, 1, stream, barrier)
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = ws * n * e2e_steps / (e2e_ms * 1e-3)
+    e2e_ms = max_over_ranks(e2e_ms, dev)
+    e2e_value = whole_job_rate(n, ws, e2e_steps, e2e_ms)
 
     fp32 = None if args.fp64_only else _fp32_legs(args, dev, stream, barrier, A)
     bwd = None if args.fp64_only else _bwd_legs(args, dev, stream, barrier)
