@@ -57,12 +57,24 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
   __shared__ double s_hx[2 * kTPB], s_hab[2 * kTPB], s_hb1[2 * kTPB], s_hb2[2 * kTPB], s_hg[2 * kTPB];
   __shared__ bool s_hcap[2 * kTPB];
   __shared__ int s_nhard;
-  // Class reorder of a tile: Lane records by slot (struct of arrays), held
-  // in s_U, which is free until phase E; owner = the matrix's row in the tile.
-  __shared__ int s_pe[kTPB], s_pmeta[kTPB];
+  // Reduced arrows of a pass (struct of arrays W, held in s_U, which is free
+  // until the staging writes): slots [0, nc) the arrows carried from the
+  // previous pass, then this tile's.  Each pass finishes a whole number of
+  // warps' worth of them and carries the rest (< 32) on, so no warp runs the
+  // zero finder and the Sec. 1.2 vectors with idle lanes; one last pass
+  // after the CTA's final tile finishes the carry.
+  constexpr int kW = kTPB + 32;
+  static_assert(7 * kW <= 9 * kTPB, "the reduced work list must fit in the staging area");
+  double* const s_w = s_U;  // 7 x kW doubles: a1 a2 b1 b2 g c s
+  __shared__ int s_we[kW];
+  __shared__ int64_t s_wg[kW];  // global index of the matrix
+  __shared__ double s_ca[7][32];
+  __shared__ int s_ce[32];
+  __shared__ int64_t s_cg[32];
+  // Rows of this tile's diagonal, deflated and non-finite matrices.
+  __shared__ int s_oth[kTPB];
   __shared__ int s_nred, s_noth;
   __shared__ alignas(8) uint64_t s_bar[2];
-  double* const s_perm = s_U;  // 7 * kTPB doubles: a1 a2 b1 b2 g c s
 
   const int tid = threadIdx.x, lane_id = tid & 31;
   const unsigned lt_mask = (1u << lane_id) - 1u;
@@ -91,48 +103,58 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
     bulk_g2s(s_in[buf], A + base * 6, bytes, &s_bar[buf]);
   };
 
+  auto lane_of_record = [&](const double* rec) {
+    const double2* src = reinterpret_cast<const double2*>(rec);
+    const double2 p0 = src[0], p1 = src[1], p2 = src[2];
+    const double a[6] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y};
+    return eispack ? make_lane<true>(a) : make_lane<false>(a);
+  };
+
   uint32_t phases = 0u;  // bit b: parity of the next completion of s_bar[b]
   int buf = 0;
+  int nc = 0;            // reduced arrows carried into this pass (CTA-uniform)
   int64_t tile = blockIdx.x;
   if (kBulkIn && tid == 0 && tile < n_tiles) issue(tile, 0);
 
-  for (; tile < n_tiles; tile += gridDim.x, buf ^= 1) {
+  for (;; tile += gridDim.x, buf ^= 1) {
+    const bool flush = (tile >= n_tiles);  // the pass that finishes the carry
+    if (flush && nc == 0) break;
     const int64_t base = tile * kTPB;
-    const int cnt = (int)((n - base) < kTPB ? (n - base) : kTPB);
+    const int cnt = flush ? 0 : (int)((n - base) < kTPB ? (n - base) : kTPB);
     const int64_t next = tile + gridDim.x;
-    if (kBulkIn) {
-      if (tid == 0 && next < n_tiles) issue(next, buf ^ 1);
-      const bool ok = mbar_wait(&s_bar[buf], (phases >> buf) & 1u);
-      if (__syncthreads_or(!ok)) {
-        // Lost wait (CTA-uniform decision): flag it, give the copies in
-        // flight a second bounded chance to land so that no write into
-        // shared memory outlives the CTA, and stop.
-        if (tid == 0) atomicOr(&g_flags, kFlagWaitTimeout);
-        mbar_wait(&s_bar[buf], (phases >> buf) & 1u);
-        if (next < n_tiles) mbar_wait(&s_bar[buf ^ 1], (phases >> (buf ^ 1)) & 1u);
-        return;
+    if (!flush) {
+      if (kBulkIn) {
+        if (tid == 0 && next < n_tiles) issue(next, buf ^ 1);
+        const bool ok = mbar_wait(&s_bar[buf], (phases >> buf) & 1u);
+        if (__syncthreads_or(!ok)) {
+          // Lost wait (CTA-uniform decision): flag it, give the copies in
+          // flight a second bounded chance to land so that no write into
+          // shared memory outlives the CTA, and stop.
+          if (tid == 0) atomicOr(&g_flags, kFlagWaitTimeout);
+          mbar_wait(&s_bar[buf], (phases >> buf) & 1u);
+          if (next < n_tiles) mbar_wait(&s_bar[buf ^ 1], (phases >> (buf ^ 1)) & 1u);
+          return;
+        }
+        phases ^= 1u << buf;
+      } else {
+        for (int i = tid; i < cnt * 6; i += kTPB) s_in[buf][i] = A[base * 6 + i];
+        __syncthreads();
       }
-      phases ^= 1u << buf;
-    } else {
-      for (int i = tid; i < cnt * 6; i += kTPB) s_in[buf][i] = A[base * 6 + i];
-      __syncthreads();
     }
 
-    // Phase A: arrow and class of the thread's own matrix.
-    Lane L;
+    // Phase A: the carried arrows take W's first slots; each thread reduces
+    // its own matrix to an arrow and classifies it; reduced arrows are
+    // appended to W, the rows of the other classes listed for phase E.
+    if (tid < nc) {
+#pragma unroll
+      for (int f = 0; f < 7; ++f) s_w[f * kW + tid] = s_ca[f][tid];
+      s_we[tid] = s_ce[tid];
+      s_wg[tid] = s_cg[tid];
+    }
     {
       Lane A0;
       A0.cls = kIdle;
-      if (tid < cnt) {
-        const double2* src = reinterpret_cast<const double2*>(&s_in[buf][tid * 6]);
-        const double2 p0 = src[0], p1 = src[1], p2 = src[2];
-        const double a[6] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y};
-        A0 = eispack ? make_lane<true>(a) : make_lane<false>(a);
-      }
-      // Reorder by class: reduced arrows take slots 0, 1, ... and the other
-      // classes slots cnt-1, cnt-2, ..., so that the warps below run either
-      // the zero finder and the Sec. 1.2 vectors or the short paths, not
-      // both with a few lanes active.  Thread t then finishes slot t.
+      if (tid < cnt) A0 = lane_of_record(&s_in[buf][tid * 6]);
       const bool red = (A0.cls == kReduced);
       const bool oth = (A0.cls != kReduced) && (A0.cls != kIdle);
       const unsigned mr = __ballot_sync(0xffffffffu, red);
@@ -144,35 +166,55 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
       }
       rb = __shfl_sync(0xffffffffu, rb, 0);
       ob = __shfl_sync(0xffffffffu, ob, 0);
-      int slot = -1;
-      if (red) slot = rb + __popc(mr & lt_mask);
-      if (oth) slot = cnt - 1 - (ob + __popc(mo & lt_mask));
-      if (slot >= 0) {
-        s_perm[0 * kTPB + slot] = A0.a1;
-        s_perm[1 * kTPB + slot] = A0.a2;
-        s_perm[2 * kTPB + slot] = A0.b1;
-        s_perm[3 * kTPB + slot] = A0.b2;
-        s_perm[4 * kTPB + slot] = A0.g;
-        s_perm[5 * kTPB + slot] = A0.c;
-        s_perm[6 * kTPB + slot] = A0.s;
-        s_pe[slot] = A0.e;
-        s_pmeta[slot] = tid | (A0.cls << 8);
+      if (red) {
+        const int slot = nc + rb + __popc(mr & lt_mask);
+        s_w[0 * kW + slot] = A0.a1;
+        s_w[1 * kW + slot] = A0.a2;
+        s_w[2 * kW + slot] = A0.b1;
+        s_w[3 * kW + slot] = A0.b2;
+        s_w[4 * kW + slot] = A0.g;
+        s_w[5 * kW + slot] = A0.c;
+        s_w[6 * kW + slot] = A0.s;
+        s_we[slot] = A0.e;
+        s_wg[slot] = base + tid;
       }
-      __syncthreads();
-      L.cls = kIdle;
-      if (tid < cnt) {
-        L.a1 = s_perm[0 * kTPB + tid];
-        L.a2 = s_perm[1 * kTPB + tid];
-        L.b1 = s_perm[2 * kTPB + tid];
-        L.b2 = s_perm[3 * kTPB + tid];
-        L.g = s_perm[4 * kTPB + tid];
-        L.c = s_perm[5 * kTPB + tid];
-        L.s = s_perm[6 * kTPB + tid];
-        L.e = s_pe[tid];
-        L.cls = s_pmeta[tid] >> 8;
+      if (oth) s_oth[ob + __popc(mo & lt_mask)] = tid;
+      if (kStudy && counters != nullptr) {
+        const unsigned md = __ballot_sync(0xffffffffu, A0.cls == kDiagonal);
+        const unsigned mf = __ballot_sync(0xffffffffu, A0.cls == kDeflated);
+        if (lane_id == 0) {
+          if (md) atomicAdd(&counters[kStatDiagonal], (unsigned long long)__popc(md));
+          if (mf) atomicAdd(&counters[kStatDeflated], (unsigned long long)__popc(mf));
+          if (mr) atomicAdd(&counters[kStatReduced], (unsigned long long)__popc(mr));
+        }
       }
     }
-    const int owner = (tid < cnt) ? (s_pmeta[tid] & 0xff) : tid;
+    __syncthreads();
+    const int n_avail = nc + s_nred, n_oth = s_noth;
+    // This pass finishes P arrows: whole warps (all of them in the last pass).
+    const int P = flush ? n_avail : min(kTPB, n_avail & ~31);
+    const int nc_next = n_avail - P;
+    if (tid < nc_next) {
+#pragma unroll
+      for (int f = 0; f < 7; ++f) s_ca[f][tid] = s_w[f * kW + P + tid];
+      s_ce[tid] = s_we[P + tid];
+      s_cg[tid] = s_wg[P + tid];
+    }
+    Lane L;
+    L.cls = kIdle;
+    int64_t gidx = -1;
+    if (tid < P) {
+      L.a1 = s_w[0 * kW + tid];
+      L.a2 = s_w[1 * kW + tid];
+      L.b1 = s_w[2 * kW + tid];
+      L.b2 = s_w[3 * kW + tid];
+      L.g = s_w[4 * kW + tid];
+      L.c = s_w[5 * kW + tid];
+      L.s = s_w[6 * kW + tid];
+      L.e = s_we[tid];
+      L.cls = kReduced;
+      gidx = s_wg[tid];
+    }
 
     // Phases B, C: FP32 seeds, then one FP64 step and the stopping test.
     // Problem 0 is mu (A - a1 I), problem 1 is nu (P(a2 I - A)P: spikes
@@ -229,7 +271,8 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
     }
 
     // Phase D: compact the unfinished roots into the shared work list and
-    // finish them with every lane of the CTA available.
+    // finish them with every lane of the CTA available.  (Its first barrier
+    // also orders every read of W above before the staging writes below.)
     int slot[2] = {-1, -1};
     {
       const unsigned m0 = __ballot_sync(0xffffffffu, hard[0]);
@@ -285,11 +328,34 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
       }
     }
 
-    // Phase E: eigenpairs, staged for the write-back.
-    bool nonfinite = false;
-    if (L.cls != kIdle) {
+    // Phase E: eigenpairs of the reduced arrow of slot tid (staged when it
+    // belongs to this tile, written straight to memory when carried in), then
+    // of one of this tile's other matrices (re-reduced from its record, which
+    // is still in shared memory).
+    if (reduced) {
       double lam[3], U[9];
-      if (L.cls == kNonFinite) {
+      finish_lane(L, root[0], root[1], lam, U);
+      const int64_t row = gidx - base;
+      if (row >= 0 && row < cnt) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s_lam[row * 3 + k] = lam[k];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) s_U[row * 9 + k] = U[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) lam_out[gidx * 3 + k] = lam[k];
+        if (want_U) {
+#pragma unroll
+          for (int k = 0; k < 9; ++k) U_out[gidx * 9 + k] = U[k];
+        }
+      }
+    }
+    bool nonfinite = false;
+    if (tid < n_oth) {
+      const int row = s_oth[tid];
+      const Lane O = lane_of_record(&s_in[buf][row * 6]);
+      double lam[3], U[9];
+      if (O.cls == kNonFinite) {
         nonfinite = true;
         const double qnan = __longlong_as_double(0x7ff8000000000000LL);
 #pragma unroll
@@ -297,12 +363,12 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
 #pragma unroll
         for (int k = 0; k < 9; ++k) U[k] = qnan;
       } else {
-        finish_lane(L, root[0], root[1], lam, U);
+        finish_lane(O, 0.0, 0.0, lam, U);
       }
 #pragma unroll
-      for (int k = 0; k < 3; ++k) s_lam[owner * 3 + k] = lam[k];
+      for (int k = 0; k < 3; ++k) s_lam[row * 3 + k] = lam[k];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) s_U[owner * 9 + k] = U[k];
+      for (int k = 0; k < 9; ++k) s_U[row * 9 + k] = U[k];
     }
     if (counters != nullptr) {
       const unsigned cm = __ballot_sync(0xffffffffu, capped);
@@ -310,16 +376,6 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
       if (lane_id == 0) {
         if (cm) atomicAdd(&counters[0], (unsigned long long)__popc(cm));
         if (nf) atomicAdd(&counters[1], (unsigned long long)__popc(nf));
-      }
-      if (kStudy) {
-        const unsigned md = __ballot_sync(0xffffffffu, L.cls == kDiagonal);
-        const unsigned mf = __ballot_sync(0xffffffffu, L.cls == kDeflated);
-        const unsigned mr = __ballot_sync(0xffffffffu, L.cls == kReduced);
-        if (lane_id == 0) {
-          if (md) atomicAdd(&counters[kStatDiagonal], (unsigned long long)__popc(md));
-          if (mf) atomicAdd(&counters[kStatDeflated], (unsigned long long)__popc(mf));
-          if (mr) atomicAdd(&counters[kStatReduced], (unsigned long long)__popc(mr));
-        }
       }
     }
     __syncthreads();
@@ -329,8 +385,9 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
       s_noth = 0;
     }
 
-    // Coalesced write-back of the tile: 16-byte stores where aligned.
-    {
+    // Coalesced write-back of the tile: 16-byte stores where aligned.  The
+    // rows of arrows carried to the next pass receive their results then.
+    if (!flush) {
       double* dst = lam_out + base * 3;
       const int m = cnt * 3;
       if (vec_lam) {
@@ -342,7 +399,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
         for (int i = tid; i < m; i += kTPB) dst[i] = s_lam[i];
       }
     }
-    if (want_U) {
+    if (!flush && want_U) {
       double* dst = U_out + base * 9;
       const int m = cnt * 9;
       if (vec_U) {
@@ -355,6 +412,8 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
       }
     }
     __syncthreads();
+    nc = nc_next;
+    if (flush) break;
   }
 }
 
