@@ -175,10 +175,10 @@ __device__ __forceinline__ void seed32x2(const float ab, const float b1[2], cons
 // right of the root (more steps needed), 2 when the start was not right of
 // the root.
 __device__ __forceinline__ int finish64(const double ab, const double b1, const double b2, const double g,
-                                        const double c, const double K, const float abf, const float b2f,
-                                        double& x) {
-  // x >= 2^-900, ab >= 2^-100 and b1, b2 >= 2^-120 (checked by the caller; abf, b2f
-  // are ab, b2 rounded to FP32): every quantity compared below is a normal
+                                        const double c, const double K, const float abf, const float b1f,
+                                        const float b2f, double& x) {
+  // x >= 2^-900, ab >= 2^-100 and b1, b2 >= 2^-120 (checked by the caller;
+  // abf, b1f, b2f are ab, b1, b2 rounded to FP32): every quantity compared below is a normal
   // positive number or a finite f, so the comparisons run on bit patterns
   // (see arith.cuh).
   const bool small = dbits(x) < dbits(ab);  // x < ab: choice of the evaluation form (see above)
@@ -186,7 +186,7 @@ __device__ __forceinline__ int finish64(const double ab, const double b1, const 
   double r1 = rcp64(x), r2 = rcp64(x + ab);
   double t1 = b1 * r1, t2 = b2 * r2;
   double f = ((x + lead) - t1) + (small ? c * x * r2 : -t2);
-  double fp = fma(t2, r2, fma(t1, r1, 1.0));  // Eq. (3)
+  const double fp = fma(t2, r2, fma(t1, r1, 1.0));  // Eq. (3)
   if (!is_pos(f)) return 2;
   // The step of Eqs. (5), (6): Delta = (f/b) S(z) with b = f' + f/x,
   // z = -4 omega_0 f / (x b^2) and S(z) = 2/(1 + sqrt(1 + z)).  Only f/b is
@@ -215,10 +215,14 @@ __device__ __forceinline__ int finish64(const double ab, const double b1, const 
   t1 = b1 * r1;
   t2 = b2 * r2;
   f = ((x + lead) - t1) + (small ? c * x * r2 : -t2);
-  fp = fma(t2, r2, fma(t1, r1, 1.0));
   if (!is_pos(f)) return 0;  // at or past the root: rounding level
   // f/f' < C eps x with C eps = 2^-51: f < 2^-51 (x f'), the product normal.
-  if (dbits(f) < dbits(x * fp) - (51ull << 52)) return 0;
+  // f' only scales the threshold: FP32 is enough, capped at 2^120 (an f'
+  // under the true one, or an FP32 x that underflowed, only makes the test
+  // stricter and leaves the root to the full iteration).
+  const float xf2 = (float)x, q1 = rcp32(xf2), q2 = rcp32(xf2 + abf);
+  const float fpf = fminf(fmaf(b2f * q2, q2, fmaf(b1f * q1, q1, 1.f)), 0x1p120f);
+  if (dbits(f) < dbits(x * (double)fpf) - (51ull << 52)) return 0;
   return 1;
 }
 
@@ -425,7 +429,7 @@ __device__ __forceinline__ void finish_lane(const Lane& L, double mu, double nu,
     v[2][0] = -gs * K.s; v[2][1] = -gc * K.s; v[2][2] = K.c;
   } else {
     // Sec. 1.2: lambda1 = a1 + mu, lambda3 = a2 - nu, trace identity for
-    // lambda2; closed-form u1, u2, u3, each normalised.
+    // lambda2; closed-form u1 and u3, normalised (u2 below).
     const double abar = a1 - a2;
     l[0] = a1 + mu;
     l[1] = (nu - mu) + g;
@@ -449,19 +453,27 @@ __device__ __forceinline__ void finish_lane(const Lane& L, double mu, double nu,
       const double inv = rsqrt(ss);
       v[k][0] *= inv; v[k][1] *= inv; v[k][2] *= inv;
     }
-    // u2 is the cross product of u1 and u3 (Sec. 1.3 relies on exactly
-    // this for its orthogonality); formed here from the normalised u1 and u3,
-    // which are unit and orthogonal to rounding, so the product is unit
-    // without a normalisation, and its error is at most the sum of theirs,
-    // each within eps / gap of its eigenvalue <= eps / (middle gap).
-    v[1][0] = fma(v[0][1], v[2][2], -v[0][2] * v[2][1]);
-    v[1][1] = fma(v[0][2], v[2][0], -v[0][0] * v[2][2]);
-    v[1][2] = fma(v[0][0], v[2][1], -v[0][1] * v[2][0]);
   }
   // Input frame: x = J v with J = [[c,-s,0],[s,c,0],[0,0,1]].
   double x00 = fma(L.c, v[0][0], -L.s * v[0][1]), x01 = fma(L.s, v[0][0], L.c * v[0][1]), x02 = v[0][2];
-  double x10 = fma(L.c, v[1][0], -L.s * v[1][1]), x11 = fma(L.s, v[1][0], L.c * v[1][1]), x12 = v[1][2];
   double x20 = fma(L.c, v[2][0], -L.s * v[2][1]), x21 = fma(L.s, v[2][0], L.c * v[2][1]), x22 = v[2][2];
+  double x10, x11, x12;
+  if (L.cls == kReduced) {
+    // u2 is the cross product of u1 and u3 (Sec. 1.3 relies on exactly
+    // this for its orthogonality); formed from the normalised u1 and u3,
+    // which are unit and orthogonal to rounding, so the product is unit
+    // without a normalisation, and its error is at most the sum of theirs,
+    // each within eps / gap of its eigenvalue <= eps / (middle gap).  J is a
+    // rotation (det 1), so J(u1 x u3) = (J u1) x (J u3): taken in the input
+    // frame directly.
+    x10 = fma(x01, x22, -x02 * x21);
+    x11 = fma(x02, x20, -x00 * x22);
+    x12 = fma(x00, x21, -x01 * x20);
+  } else {
+    x10 = fma(L.c, v[1][0], -L.s * v[1][1]);
+    x11 = fma(L.s, v[1][0], L.c * v[1][1]);
+    x12 = v[1][2];
+  }
   double l0 = l[0], l1 = l[1], l2 = l[2];
   // Ascending and stable (strict comparisons keep equal eigenvalues in the
   // order above): three compare-and-swap steps on registers.
