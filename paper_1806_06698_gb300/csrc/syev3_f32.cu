@@ -549,25 +549,29 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
         }
         double lam[3], U[9];
         f64::finish_lane(D, mu, nu, lam, U);  // eigenvectors re-formed in FP64
-        // FP64 residual check against the input record.
-        const float* rec = &s_in[buf][owner * 6];
-        const double M[3][3] = {{rec[0], rec[3], rec[4]}, {rec[3], rec[1], rec[5]}, {rec[4], rec[5], rec[2]}};
-        double nA = 0.0, worst = 0.0;
+        // FP64 residual check against the input record, for counter [3]
+        // (skipped when no counters are asked for: it is a diagnostic).
+        if (counters != nullptr) {
+          const float* rec = &s_in[buf][owner * 6];
+          const double M[3][3] = {{rec[0], rec[3], rec[4]}, {rec[3], rec[1], rec[5]}, {rec[4], rec[5], rec[2]}};
+          double nA = 0.0, worst = 0.0;
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+          for (int r = 0; r < 3; ++r)
 #pragma unroll
-          for (int q = 0; q < 3; ++q) nA = fma(M[r][q], M[r][q], nA);
+            for (int q = 0; q < 3; ++q) nA = fma(M[r][q], M[r][q], nA);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          double rr = 0.0;
+          for (int k = 0; k < 3; ++k) {
+            double rr = 0.0;
 #pragma unroll
-          for (int r = 0; r < 3; ++r) {
-            const double v = fma(M[r][0], U[k], fma(M[r][1], U[3 + k], fma(M[r][2], U[6 + k], -lam[k] * U[r * 3 + k])));
-            rr = fma(v, v, rr);
+            for (int r = 0; r < 3; ++r) {
+              const double v =
+                  fma(M[r][0], U[k], fma(M[r][1], U[3 + k], fma(M[r][2], U[6 + k], -lam[k] * U[r * 3 + k])));
+              rr = fma(v, v, rr);
+            }
+            worst = fmax(worst, rr);
           }
-          worst = fmax(worst, rr);
+          if (!(worst <= kResidualTol * kResidualTol * nA)) atomicAdd(&counters[3], 1ull);
         }
-        if (counters != nullptr && !(worst <= kResidualTol * kResidualTol * nA)) atomicAdd(&counters[3], 1ull);
 #pragma unroll
         for (int k = 0; k < 3; ++k) s_lam[owner * 3 + k] = (float)lam[k];
 #pragma unroll
