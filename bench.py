@@ -54,6 +54,8 @@ TRAFFIC_CASES = {
     "f64": ("k_syev3_f64", ["syev3_f64.cu", "solve_f64.cuh"] + _COMMON, "mixed FP64"),
     "f32": ("k_syev3_f32", ["syev3_f32.cu", "solve_f64.cuh"] + _COMMON, "mixed FP32, plain"),
     "f32c": ("k_syev3_f32", ["syev3_f32.cu", "solve_f64.cuh"] + _COMMON, "mixed FP32, compensated"),
+    "f32ws": ("k_syev3_f32", ["syev3_f32.cu", "solve_f64.cuh", "syev3_api.cu"] + _COMMON,
+              "mixed FP32, compensated through syev3_batched_ws (FP32 kernel; the refinement kernel is k_refine_f32)"),
     "bwd64": ("k_syev3_bwd", ["syev3_bwd.cu"] + _COMMON, "spectral FP64 backward"),
     "bwd32": ("k_syev3_bwd", ["syev3_bwd.cu"] + _COMMON, "spectral FP32 backward"),
 }
@@ -292,15 +294,20 @@ def _fp32_legs(args, dev, stream, barrier, A64_dev):
         lam_ref, _ = syev3.syev3_batched(A_ref, stream=stream)
         lam_ref_h = lam_ref.cpu().numpy()
         nrm_h = np.linalg.norm(lam_ref_h, axis=1)
-        for mode in ("plain", "compensated"):
-            comp = mode == "compensated"
+        # compensated: syev3_batched_ws (the FP64 refinement as a second
+        # kernel over a list in a workspace); compensated_single_kernel:
+        # syev3_batched (the refinement inside the FP32 kernel).
+        ws = torch.empty(syev3.workspace_bytes(n, torch.float32, compensated=True), dtype=torch.uint8, device=dev)
+        for mode in ("plain", "compensated", "compensated_single_kernel"):
+            comp = mode != "plain"
+            work = ws if mode == "compensated" else None
             ctr = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device=dev)
 
             def step():
-                syev3.syev3_batched(A, out=(lam, U), compensated=comp, stream=stream)
+                syev3.syev3_batched(A, out=(lam, U), compensated=comp, workspace=work, stream=stream)
 
             total_ms, kms = _timed(step, args.steps, args.warmup, stream, barrier)
-            syev3.syev3_batched(A, out=(lam, U), compensated=comp, counters=ctr, stream=stream)
+            syev3.syev3_batched(A, out=(lam, U), compensated=comp, counters=ctr, workspace=work, stream=stream)
             barrier()
             # Accuracy on the host (no library GEMM in the bench's launch list).
             lam_s, U_s = lam[idx].double().cpu().numpy(), U[idx].double().cpu().numpy()
@@ -312,14 +319,15 @@ def _fp32_legs(args, dev, stream, barrier, A64_dev):
                 "value": n * args.steps / (total_ms * 1e-3), "unit": UNIT, "ms_per_step": total_ms / args.steps,
                 "dtype": "f32", "n": n,
                 "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                             "traffic": traffic_per_launch("f32c" if comp else "f32", n),
-                             "kernel": "k_syev3_f32", "peak_source": "MEASURED_PEAKS hbm_gbs"},
+                             "traffic": traffic_per_launch({"plain": "f32", "compensated": "f32ws"}.get(mode, "f32c"), n),
+                             "kernel": "k_syev3_f32" + (" + k_refine_f32" if work is not None else ""),
+                             "peak_source": "MEASURED_PEAKS hbm_gbs"},
                 "fp64_refined_fraction": ctr[2].item() / n if comp else 0.0,
                 "max_dlambda_vs_fp64_kernel_eps32": dl / 2.0 ** -23,
                 "max_orthogonality_eps32": orth / 2.0 ** -23,
                 "accuracy_sample": int(idx.numel()),
             }
-        del A, lam, U, A_ref
+        del A, lam, U, A_ref, ws
         torch.cuda.empty_cache()
     return out
 
@@ -666,7 +674,7 @@ def _profile_inputs(case: str, n: int):
 
     if case == "f64":
         return inputs.mixed(n, seed=inputs.SEED_BASE + 1)[0]
-    if case in ("f32", "f32c"):
+    if case in ("f32", "f32c", "f32ws"):
         return inputs.mixed_fp32(n)[0]
     return inputs.spectral(n, seed=inputs.SEED_BASE + 4)[0]
 
@@ -683,11 +691,14 @@ def run_profile_case(args):
     case, n = args.profile_case, args.n
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
-    dt = torch.float32 if case in ("f32", "f32c", "bwd32") else torch.float64
+    dt = torch.float32 if case in ("f32", "f32c", "f32ws", "bwd32") else torch.float64
     A = torch.from_numpy(_profile_inputs(case, n)).to(dev, dt)
     lam = torch.empty((n, 3), dtype=dt, device=dev)
     U = torch.empty((n, 3, 3), dtype=dt, device=dev)
-    syev3.syev3_batched(A, out=(lam, U), compensated=(case == "f32c"), stream=stream)
+    ws = None
+    if case == "f32ws":
+        ws = torch.empty(syev3.workspace_bytes(n, dt, compensated=True), dtype=torch.uint8, device=dev)
+    syev3.syev3_batched(A, out=(lam, U), compensated=case in ("f32c", "f32ws"), workspace=ws, stream=stream)
     if case.startswith("bwd"):
         rng = np.random.default_rng(1806066986)
         w = torch.from_numpy(rng.standard_normal((n, 3))).to(dev, dt)

@@ -76,8 +76,10 @@ int syev3_last_cuda_error(void);
  *   stream    : CUDA stream the work is ordered on.
  * Returns SYEV3_EINVAL (NULL A or lambda, n < 0, bad dtype, misaligned or
  * overlapping buffers) or SYEV3_ECUDA (launch failure); SYEV3_OK otherwise.
- * No entry point allocates device memory: the FP64 refinement of the
- * compensated FP32 form works on a shared-memory list inside the kernel.
+ * syev3_batched allocates no device memory and uses none beyond its
+ * arguments: the FP64 refinement of the compensated FP32 form works on a
+ * shared-memory list inside the kernel (syev3_batched_ws takes a scratch
+ * workspace from the caller instead).
  */
 int syev3_batched(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype,
                   syev3_stream_t stream);
@@ -93,6 +95,27 @@ int syev3_batched(const void* A_packed6, int64_t n, void* lambda, void* U, int d
  */
 int syev3_batched_ex(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype,
                      uint64_t* d_counters, syev3_stream_t stream);
+
+/* syev3_batched_ws -- syev3_batched_ex with a caller-provided device
+ * workspace.  For SYEV3_F32_COMPENSATED the FP64 refinement of flagged lanes
+ * (not in the paper: see SYEV3_F32_COMPENSATED) then runs as a second kernel
+ * over a list of those lanes kept in the workspace, so the FP32 kernel holds
+ * no FP64 code (fewer registers, more resident warps) and the refinement
+ * runs in full warps; results equal those of syev3_batched up to rounding.
+ * Other dtypes ignore the workspace (it may be NULL).
+ *   d_workspace     : device, at least syev3_workspace_bytes(n, dtype) bytes,
+ *                     256-byte aligned, caller-owned; must not overlap the
+ *                     inputs or outputs; contents need not be initialised
+ *                     (the library clears what must start at zero on
+ *                     `stream`).  Calls that share a workspace must be
+ *                     ordered (same stream or synchronised).
+ *   workspace_bytes : its size.
+ * Returns SYEV3_EINVAL as syev3_batched_ex, and for a missing, misaligned,
+ * too small, host-pageable or overlapping workspace. */
+size_t syev3_workspace_bytes(int64_t n, int dtype);
+
+int syev3_batched_ws(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype, uint64_t* d_counters,
+                     void* d_workspace, size_t workspace_bytes, syev3_stream_t stream);
 
 /* syev3_batched_method -- syev3_batched (FP64 only) with the variants of
  * the method the paper also describes, for studying them against the

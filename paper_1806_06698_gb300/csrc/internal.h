@@ -31,6 +31,20 @@ cudaError_t launch_f64_method(const double* A, int64_t n, double* lam, double* U
 cudaError_t launch_f32(const float* A, int64_t n, float* lam, float* U, bool compensated,
                        unsigned long long* counters, cudaStream_t stream);
 
+// Compensated FP32 with the refinement deferred to a second kernel
+// (syev3_batched_ws): the workspace holds a counter at offset 0 and, from
+// kFlagListOffset, up to n records of flagged lanes.
+struct alignas(16) FlagRec {
+  float v[9];       // a1 a2 b1 b2 g c s (pre-scaled arrow and rotation), mu, nu
+  int code;         // e << 2 | class
+  long long gidx;   // index of the matrix in the batch
+};
+static_assert(sizeof(FlagRec) == 48, "FlagRec layout");
+constexpr size_t kFlagListOffset = 256;
+size_t f32c_workspace_bytes(int64_t n);
+cudaError_t launch_f32c_deferred(const float* A, int64_t n, float* lam, float* U, unsigned long long* counters,
+                                 void* work, cudaStream_t stream);
+
 template <class T>
 cudaError_t launch_bwd(const T* lam, const T* U, const T* gl, const T* gU, int64_t n, T* gA, T tau,
                        cudaStream_t stream);

@@ -103,6 +103,31 @@ int syev3_batched(const void* A_packed6, int64_t n, void* lambda, void* U, int d
   return syev3_batched_ex(A_packed6, n, lambda, U, dtype, nullptr, stream);
 }
 
+size_t syev3_workspace_bytes(int64_t n, int dtype) {
+  if (n <= 0 || dtype != SYEV3_F32_COMPENSATED) return 0;
+  return syev3::f32c_workspace_bytes(n);
+}
+
+int syev3_batched_ws(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype, uint64_t* d_counters,
+                     void* d_workspace, size_t workspace_bytes, syev3_stream_t stream) {
+  if (dtype != SYEV3_F32_COMPENSATED)
+    return syev3_batched_ex(A_packed6, n, lambda, U, dtype, d_counters, stream);
+  const int st = check_forward(A_packed6, n, lambda, U, dtype);
+  if (st != SYEV3_OK || n == 0) return st;
+  if (d_counters && (!aligned(d_counters, 8) || !device_accessible(d_counters))) return SYEV3_EINVAL;
+  const size_t need = syev3::f32c_workspace_bytes(n);
+  if (d_workspace == nullptr || workspace_bytes < need || !aligned(d_workspace, 256) ||
+      !device_accessible(d_workspace))
+    return SYEV3_EINVAL;
+  if (overlap(d_workspace, need, A_packed6, (size_t)n * 24) || overlap(d_workspace, need, lambda, (size_t)n * 12) ||
+      overlap(d_workspace, need, U, (size_t)n * 36))
+    return SYEV3_EINVAL;
+  const cudaError_t e = syev3::launch_f32c_deferred(
+      static_cast<const float*>(A_packed6), n, static_cast<float*>(lambda), static_cast<float*>(U),
+      reinterpret_cast<unsigned long long*>(d_counters), d_workspace, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SYEV3_OK : cuda_fail(e);
+}
+
 int syev3_batched_method(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype,
                          const syev3_method* method, uint64_t* d_stats, syev3_stream_t stream) {
   if (dtype != SYEV3_F64 || method == nullptr) return SYEV3_EINVAL;

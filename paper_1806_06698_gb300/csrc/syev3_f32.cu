@@ -45,6 +45,7 @@ constexpr float kTinySpike32 = 0x1p-60f;  // spikes below this are zeroed (beta-
 constexpr float kNearDefl = 16.0f;        // near-deflated: test sides within this factor
 constexpr float kClusterTau = 0x1p-16f;   // clustered: relative gap below this
 constexpr double kResidualTol = 16.0 * 0x1p-23;  // FP64 residual check, times ||A||_F
+constexpr int kPlain = 0, kInline = 1, kDeferred = 2;  // modes of k_syev3_f32
 
 constexpr int kDiag = f64::kDiagonal, kDefl = f64::kDeflated, kRed = f64::kReduced,
               kNonFin = f64::kNonFinite, kIdle = f64::kIdle;
@@ -337,16 +338,66 @@ __device__ __forceinline__ float unscale32(float v, int e) {
   return (e >= -126 && e <= 127) ? v * pow2f(e) : scalbnf(v, e);
 }
 
-template <bool kBulkIn, bool kComp>
+// FP64 refinement of one flagged lane (compensated form): the arrow and the
+// FP32 roots f[0..8] = (a1, a2, b1, b2, g, c, s, mu, nu), code = e << 2 | cls.
+// A final FP64 Newton step on mu and nu (Sec. 1.4.2), eigenvectors re-formed
+// in FP64; with `rec` (the input record), the FP64 residual check
+// ||A u - lambda u|| <= 16 eps32 ||A||_F, whose failure is returned.
+__device__ __forceinline__ bool refine_one(const float f[9], const int code, const float* rec, double lam[3],
+                                        double U[9]) {
+  f64::Lane D;
+  D.a1 = f[0]; D.a2 = f[1]; D.b1 = f[2]; D.b2 = f[3]; D.g = f[4]; D.c = f[5]; D.s = f[6];
+  D.cls = code & 3;
+  D.e = code >> 2;
+  double mu = f[7], nu = f[8];
+  if (D.cls == kRed) {
+    const double ab = D.a1 - D.a2, bb1 = D.b1 * D.b1, bb2 = D.b2 * D.b2;
+    const double rab = rcp64(ab);
+    const double g0 = D.g - D.a1, g1 = D.a2 - D.g;
+    const double c0 = bb2 * rab, c1 = bb1 * rab;
+    if (mu > 0.0) mu = f64::newton64(ab, bb1, bb2, g0, c0, -g0 - c0, mu);
+    if (nu > 0.0) nu = f64::newton64(ab, bb2, bb1, g1, c1, -g1 - c1, nu);
+  }
+  f64::finish_lane(D, mu, nu, lam, U);
+  if (rec == nullptr) return false;
+  const double M[3][3] = {{rec[0], rec[3], rec[4]}, {rec[3], rec[1], rec[5]}, {rec[4], rec[5], rec[2]}};
+  double nA = 0.0, worst = 0.0;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) nA = fma(M[r][q], M[r][q], nA);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double rr = 0.0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const double v = fma(M[r][0], U[k], fma(M[r][1], U[3 + k], fma(M[r][2], U[6 + k], -lam[k] * U[r * 3 + k])));
+      rr = fma(v, v, rr);
+    }
+    worst = fmax(worst, rr);
+  }
+  return !(worst <= kResidualTol * kResidualTol * nA);
+}
+
+// kMode: kPlain (SYEV3_F32), kInline (compensated, flagged lanes refined in
+// FP64 inside the kernel on a shared-memory list) or kDeferred (compensated,
+// flagged lanes appended to a list in global memory -- the workspace of
+// syev3_batched_ws -- and refined by k_refine_f32; the kernel then holds no
+// FP64 code and needs fewer registers).
+template <bool kBulkIn, int kMode>
 __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A, int64_t n,
                                                     float* __restrict__ lam_out, float* __restrict__ U_out,
-                                                    unsigned long long* __restrict__ counters) {
+                                                    unsigned long long* __restrict__ counters,
+                                                    FlagRec* __restrict__ flag_list,
+                                                    unsigned long long* __restrict__ flag_count) {
+  constexpr bool kComp = kMode != kPlain;
+  constexpr bool kDefer = kMode == kDeferred;
   __shared__ alignas(16) float s_in[2][kTPB * 6];
   __shared__ alignas(16) float s_lam[kTPB * 3];
   __shared__ alignas(16) float s_U[kTPB * 9];
   // Compensated form: flagged lanes for the FP64 refinement (arrow, roots, owner).
-  __shared__ float s_fa[kComp ? 9 * kTPB : 1];
-  __shared__ int s_fi[kComp ? 2 * kTPB : 1];
+  __shared__ float s_fa[kMode == kInline ? 9 * kTPB : 1];
+  __shared__ int s_fi[kMode == kInline ? 2 * kTPB : 1];
   __shared__ int s_nflag;
   // Roots that need more steps than the fixed schedule: (ab, b1, b2, g, x).
   __shared__ float s_more[2 * kTPB * 5];
@@ -513,7 +564,22 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
       for (int k = 0; k < 9; ++k) s_U[tid * 9 + k] = U[k];
     }
 
-    if (kComp) {
+    if (kDefer) {
+      // Append the flagged lanes to the global list (one atomic per warp);
+      // k_refine_f32 refines them and overwrites their outputs.
+      const unsigned m = __ballot_sync(0xffffffffu, flagged);
+      unsigned long long wbase = 0;
+      if (lane_id == 0 && m) wbase = atomicAdd(flag_count, (unsigned long long)__popc(m));
+      wbase = __shfl_sync(0xffffffffu, wbase, 0);
+      if (flagged) {
+        FlagRec r;
+        r.v[0] = L.a1; r.v[1] = L.a2; r.v[2] = L.b1; r.v[3] = L.b2; r.v[4] = L.g; r.v[5] = L.c; r.v[6] = L.s;
+        r.v[7] = root[0]; r.v[8] = root[1];
+        r.code = (L.e << 2) | L.cls;
+        r.gidx = base + tid;
+        flag_list[wbase + __popc(m & lt_mask)] = r;
+      }
+    } else if (kComp) {
       // Compact the flagged lanes and refine them in FP64 with every lane of
       // the CTA available.
       const unsigned m = __ballot_sync(0xffffffffu, flagged);
@@ -531,47 +597,12 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
       __syncthreads();
       const int nf = s_nflag;
       for (int i = tid; i < nf; i += kTPB) {
-        const float* f = &s_fa[i * 9];
-        const int owner = s_fi[i * 2], code = s_fi[i * 2 + 1];
-        f64::Lane D;
-        D.a1 = f[0]; D.a2 = f[1]; D.b1 = f[2]; D.b2 = f[3]; D.g = f[4]; D.c = f[5]; D.s = f[6];
-        D.cls = code & 3;
-        D.e = code >> 2;
-        double mu = f[7], nu = f[8];
-        if (D.cls == kRed) {
-          // Final FP64 Newton step on mu and nu (Sec. 1.4.2).
-          const double ab = D.a1 - D.a2, bb1 = D.b1 * D.b1, bb2 = D.b2 * D.b2;
-          const double rab = rcp64(ab);
-          const double g0 = D.g - D.a1, g1 = D.a2 - D.g;
-          const double c0 = bb2 * rab, c1 = bb1 * rab;
-          if (mu > 0.0) mu = f64::newton64(ab, bb1, bb2, g0, c0, -g0 - c0, mu);
-          if (nu > 0.0) nu = f64::newton64(ab, bb2, bb1, g1, c1, -g1 - c1, nu);
-        }
+        const int owner = s_fi[i * 2];
         double lam[3], U[9];
-        f64::finish_lane(D, mu, nu, lam, U);  // eigenvectors re-formed in FP64
-        // FP64 residual check against the input record, for counter [3]
-        // (skipped when no counters are asked for: it is a diagnostic).
-        if (counters != nullptr) {
-          const float* rec = &s_in[buf][owner * 6];
-          const double M[3][3] = {{rec[0], rec[3], rec[4]}, {rec[3], rec[1], rec[5]}, {rec[4], rec[5], rec[2]}};
-          double nA = 0.0, worst = 0.0;
-#pragma unroll
-          for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int q = 0; q < 3; ++q) nA = fma(M[r][q], M[r][q], nA);
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            double rr = 0.0;
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-              const double v =
-                  fma(M[r][0], U[k], fma(M[r][1], U[3 + k], fma(M[r][2], U[6 + k], -lam[k] * U[r * 3 + k])));
-              rr = fma(v, v, rr);
-            }
-            worst = fmax(worst, rr);
-          }
-          if (!(worst <= kResidualTol * kResidualTol * nA)) atomicAdd(&counters[3], 1ull);
-        }
+        // The residual check (counter [3]) only when counters are asked for.
+        const bool bad = refine_one(&s_fa[i * 9], s_fi[i * 2 + 1],
+                                    counters != nullptr ? &s_in[buf][owner * 6] : nullptr, lam, U);
+        if (bad) atomicAdd(&counters[3], 1ull);
 #pragma unroll
         for (int k = 0; k < 3; ++k) s_lam[owner * 3 + k] = (float)lam[k];
 #pragma unroll
@@ -622,25 +653,60 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
   }
 }
 
-template <bool kBulkIn, bool kComp>
+template <bool kBulkIn, int kMode>
 int blocks_per_sm_f32() {
   static int cached = -1;
   if (cached < 0) {
     int v = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_syev3_f32<kBulkIn, kComp>, kTPB, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_syev3_f32<kBulkIn, kMode>, kTPB, 0);
     cached = (e == cudaSuccess && v > 0) ? v : 1;
   }
   return cached;
 }
 
-template <bool kBulkIn, bool kComp>
+template <bool kBulkIn, int kMode>
 cudaError_t launch(const float* A, int64_t n, float* lam, float* U, unsigned long long* counters,
-                   cudaStream_t stream, int sms) {
+                   FlagRec* flag_list, unsigned long long* flag_count, cudaStream_t stream, int sms) {
   const int64_t n_tiles = (n + kTPB - 1) / kTPB;
-  const int64_t resident = (int64_t)sms * blocks_per_sm_f32<kBulkIn, kComp>();
+  const int64_t resident = (int64_t)sms * blocks_per_sm_f32<kBulkIn, kMode>();
   const int grid = (int)(n_tiles < resident ? n_tiles : resident);
-  k_syev3_f32<kBulkIn, kComp><<<grid, kTPB, 0, stream>>>(A, n, lam, U, counters);
+  k_syev3_f32<kBulkIn, kMode><<<grid, kTPB, 0, stream>>>(A, n, lam, U, counters, flag_list, flag_count);
   return cudaGetLastError();
+}
+
+// The refinement of the deferred compensated form: one flagged lane per
+// thread, grid-stride over the list (its length is read on the device).
+constexpr int kRefineTPB = 128;
+
+__global__ void __launch_bounds__(kRefineTPB) k_refine_f32(const FlagRec* __restrict__ list,
+                                                           const unsigned long long* __restrict__ count,
+                                                           const float* __restrict__ A, float* __restrict__ lam_out,
+                                                           float* __restrict__ U_out,
+                                                           unsigned long long* __restrict__ counters) {
+  const unsigned long long m = *count;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * kRefineTPB + threadIdx.x; i < m;
+       i += (unsigned long long)gridDim.x * kRefineTPB) {
+    const FlagRec r = list[i];
+    double lam[3], U[9];
+    const bool bad = refine_one(r.v, r.code, counters != nullptr ? A + r.gidx * 6 : nullptr, lam, U);
+    if (bad) atomicAdd(&counters[3], 1ull);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) lam_out[r.gidx * 3 + k] = (float)lam[k];
+    if (U_out != nullptr) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) U_out[r.gidx * 9 + k] = (float)U[k];
+    }
+  }
+}
+
+int refine_blocks_per_sm() {
+  static int cached = -1;
+  if (cached < 0) {
+    int v = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_refine_f32, kRefineTPB, 0);
+    cached = (e == cudaSuccess && v > 0) ? v : 1;
+  }
+  return cached;
 }
 
 }  // namespace
@@ -655,10 +721,32 @@ cudaError_t launch_f32(const float* A, int64_t n, float* lam, float* U, bool com
   if (e != cudaSuccess) return e;
   const bool bulk = (reinterpret_cast<uintptr_t>(A) & 15) == 0;
   if (bulk)
-    return compensated ? launch<true, true>(A, n, lam, U, counters, stream, sms)
-                       : launch<true, false>(A, n, lam, U, counters, stream, sms);
-  return compensated ? launch<false, true>(A, n, lam, U, counters, stream, sms)
-                     : launch<false, false>(A, n, lam, U, counters, stream, sms);
+    return compensated ? launch<true, kInline>(A, n, lam, U, counters, nullptr, nullptr, stream, sms)
+                       : launch<true, kPlain>(A, n, lam, U, counters, nullptr, nullptr, stream, sms);
+  return compensated ? launch<false, kInline>(A, n, lam, U, counters, nullptr, nullptr, stream, sms)
+                     : launch<false, kPlain>(A, n, lam, U, counters, nullptr, nullptr, stream, sms);
+}
+
+size_t f32c_workspace_bytes(int64_t n) { return kFlagListOffset + (size_t)n * sizeof(FlagRec); }
+
+cudaError_t launch_f32c_deferred(const float* A, int64_t n, float* lam, float* U, unsigned long long* counters,
+                                 void* work, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  auto* count = static_cast<unsigned long long*>(work);
+  auto* list = reinterpret_cast<FlagRec*>(static_cast<char*>(work) + kFlagListOffset);
+  e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  e = ((reinterpret_cast<uintptr_t>(A) & 15) == 0)
+          ? launch<true, kDeferred>(A, n, lam, U, counters, list, count, stream, sms)
+          : launch<false, kDeferred>(A, n, lam, U, counters, list, count, stream, sms);
+  if (e != cudaSuccess) return e;
+  k_refine_f32<<<sms * refine_blocks_per_sm(), kRefineTPB, 0, stream>>>(list, count, A, lam, U, counters);
+  return cudaGetLastError();
 }
 
 cudaError_t take_flags_f32(unsigned* flags) {

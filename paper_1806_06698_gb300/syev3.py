@@ -59,6 +59,10 @@ def _load():
             lib.syev3_batched_ex.restype = i32
             lib.syev3_batched_method.argtypes = [vp, i64, vp, vp, i32, ctypes.POINTER(_Method), vp, vp]
             lib.syev3_batched_method.restype = i32
+            lib.syev3_workspace_bytes.argtypes = [i64, i32]
+            lib.syev3_workspace_bytes.restype = ctypes.c_size_t
+            lib.syev3_batched_ws.argtypes = [vp, i64, vp, vp, i32, vp, vp, ctypes.c_size_t, vp]
+            lib.syev3_batched_ws.restype = i32
             lib.syev3_batched_bwd.argtypes = [vp, vp, vp, vp, i64, vp, ctypes.c_double, i32, vp]
             lib.syev3_batched_bwd.restype = i32
             lib.syev3_batched_host.argtypes = [vp, i64, vp, vp, i32, i64, vp]
@@ -98,13 +102,20 @@ def dtype_code(dtype: torch.dtype, compensated: bool = False) -> int:
     raise ValueError(f"unsupported dtype {dtype}")
 
 
+def workspace_bytes(n: int, dtype: torch.dtype, compensated: bool = False) -> int:
+    """Bytes of device workspace syev3_batched(..., workspace=...) needs."""
+    return int(_load().syev3_workspace_bytes(int(n), dtype_code(dtype, compensated)))
+
+
 def syev3_batched(A6: torch.Tensor, *, vectors: bool = True, compensated: bool = False,
                   out: tuple[torch.Tensor, torch.Tensor | None] | None = None,
-                  counters: torch.Tensor | None = None, stream=None):
+                  counters: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None):
     """Eigenvalues (n,3) ascending and eigenvectors (n,3,3) (columns) of the
     packed symmetric matrices ``A6`` (n,6) on the GPU.  ``counters`` is an
     optional uint64-sized (int64) device tensor of 4 entries the kernels add
-    to (see include/syev3.h)."""
+    to (see include/syev3.h).  ``workspace`` (a device tensor of at least
+    workspace_bytes(...) bytes) selects syev3_batched_ws: for the compensated
+    form, the FP64 refinement as a second kernel."""
     if not A6.is_cuda:
         raise ValueError("A6 must be a CUDA tensor (no CPU fallback)")
     if A6.dim() != 2 or A6.shape[1] != 6 or not A6.is_contiguous():
@@ -117,7 +128,10 @@ def syev3_batched(A6: torch.Tensor, *, vectors: bool = True, compensated: bool =
     else:
         lam, U = out
     lib = _load()
-    if counters is None:
+    if workspace is not None:
+        st = lib.syev3_batched_ws(_ptr(A6), n, _ptr(lam), _ptr(U), code, _ptr(counters), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _stream(stream))
+    elif counters is None:
         st = lib.syev3_batched(_ptr(A6), n, _ptr(lam), _ptr(U), code, _stream(stream))
     else:
         st = lib.syev3_batched_ex(_ptr(A6), n, _ptr(lam), _ptr(U), code, _ptr(counters), _stream(stream))

@@ -85,3 +85,27 @@ def test_method_entry_point_argument_checks(lib):
     assert call(dummy, -1, vp(8192), None, syev3.SYEV3_F64, ctypes.byref(ok), None, None) == syev3.SYEV3_EINVAL
     assert call(None, 0, None, None, syev3.SYEV3_F64, ctypes.byref(ok), None, None) == syev3.SYEV3_OK
     assert len(syev3.METHOD_STATS) == 8
+
+
+def test_workspace_entry_point_argument_checks(lib):
+    from paper_1806_06698_gb300 import syev3
+
+    vp = ctypes.c_void_p
+    # the workspace is needed by the compensated form only
+    assert lib.syev3_workspace_bytes(1000, syev3.SYEV3_F64) == 0
+    assert lib.syev3_workspace_bytes(1000, syev3.SYEV3_F32) == 0
+    need = lib.syev3_workspace_bytes(1000, syev3.SYEV3_F32_COMPENSATED)
+    assert need >= 1000 * 48
+    assert lib.syev3_workspace_bytes(0, syev3.SYEV3_F32_COMPENSATED) == 0
+    call = lib.syev3_batched_ws
+    A, lam = vp(1 << 20), vp(2 << 20)
+    # missing, too small or misaligned workspace: EINVAL before any CUDA call
+    assert call(A, 1000, lam, None, syev3.SYEV3_F32_COMPENSATED, None, None, 0, None) == syev3.SYEV3_EINVAL
+    assert call(A, 1000, lam, None, syev3.SYEV3_F32_COMPENSATED, None, vp(4 << 20), need - 1,
+                None) == syev3.SYEV3_EINVAL
+    assert call(A, 1000, lam, None, syev3.SYEV3_F32_COMPENSATED, None, vp((4 << 20) + 16), need,
+                None) == syev3.SYEV3_EINVAL
+    # overlapping the input
+    assert call(A, 1000, lam, None, syev3.SYEV3_F32_COMPENSATED, None, A, need, None) == syev3.SYEV3_EINVAL
+    # n == 0 is a no-op
+    assert call(None, 0, None, None, syev3.SYEV3_F32_COMPENSATED, None, None, 0, None) == syev3.SYEV3_OK

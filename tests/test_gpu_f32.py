@@ -19,7 +19,18 @@ pytestmark = pytest.mark.gpu
 
 from paper_1806_06698_gb300 import inputs  # noqa: E402
 
-MODES = ["plain", "compensated"]
+# "workspace": the compensated form through syev3_batched_ws (its FP64
+# refinement as a second kernel over a list in a caller-provided workspace).
+MODES = ["plain", "compensated", "workspace"]
+
+
+def solve(mod, A_t, mode, **kw):
+    comp = mode in ("compensated", "workspace")
+    ws = None
+    if mode == "workspace":
+        nb = mod.workspace_bytes(A_t.shape[0], A_t.dtype, compensated=True)
+        ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=A_t.device)
+    return mod.syev3_batched(A_t, compensated=comp, workspace=ws, **kw)
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +45,7 @@ def syev3():
 
 def run32(mod, A32, mode, counters=None, vectors=True):
     A = torch.from_numpy(np.ascontiguousarray(A32, dtype=np.float32)).cuda()
-    lam, U = mod.syev3_batched(A, vectors=vectors, compensated=(mode == "compensated"), counters=counters)
+    lam, U = solve(mod, A, mode, vectors=vectors, counters=counters)
     torch.cuda.synchronize()
     return lam.cpu().numpy(), (U.cpu().numpy() if U is not None else None)
 
@@ -87,7 +98,7 @@ def test_mixed_fp32_subsets(syev3, mode):
         vec_gap_filtered_compare(A[m], lam[m], U[m], lam_o[m], U_o[m])
     c = ctr.cpu().numpy()
     assert c[0] == 0 and c[1] == 0 and c[3] == 0
-    if mode == "compensated":
+    if mode != "plain":
         assert c[2] > 0  # the clustered subset is flagged for FP64 refinement
     else:
         assert c[2] == 0
@@ -127,7 +138,7 @@ def test_unaligned_and_eigenvalues_only(syev3, mode):
     lam_b = torch.zeros(999 * 3 + 1, dtype=torch.float32, device="cuda")
     U_b = torch.zeros(999 * 9 + 1, dtype=torch.float32, device="cuda")
     lam_v, U_v = lam_b[1:].view(999, 3), U_b[1:].view(999, 3, 3)
-    syev3.syev3_batched(buf[1:].view(999, 6), out=(lam_v, U_v), compensated=(mode == "compensated"))
+    solve(syev3, buf[1:].view(999, 6), mode, out=(lam_v, U_v))
     torch.cuda.synchronize()
     lam_o, U_o = oracle.syev3(A.astype(np.float64))
     vec_gap_filtered_compare(A, lam_v.cpu().numpy(), U_v.cpu().numpy(), lam_o, U_o)
@@ -145,7 +156,7 @@ def test_full_size_fp32_sampled(syev3, mode):
         n = A.shape[0]
         At = torch.from_numpy(A).cuda()
         ctr = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device="cuda")
-        lam, U = syev3.syev3_batched(At, compensated=(mode == "compensated"), counters=ctr)
+        lam, U = solve(syev3, At, mode, counters=ctr)
         torch.cuda.synchronize()
         c = ctr.cpu().numpy()
         assert c[0] == 0 and c[1] == 0 and c[3] == 0
@@ -191,3 +202,33 @@ def test_precision_report(syev3, capsys):
             assert dl.max() <= 64 and res.max() <= 64 and orth.max() <= 64
     with capsys.disabled():
         print("\n" + "\n".join(lines))
+
+
+def test_workspace_path_matches_single_kernel(syev3):
+    """syev3_batched_ws (refinement as a second kernel) against syev3_batched
+    (refinement inside the kernel) on the same inputs, twice in a row on one
+    workspace (the list's counter is cleared by each call): the same
+    refinement code, so equal up to the compiler's contraction choices, and
+    the same counters; the workspace checks of the C ABI on real buffers."""
+    A, _ = inputs.mixed_fp32(1 << 15, seed=2111)
+    At = torch.from_numpy(A).cuda()
+    c1 = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device="cuda")
+    lam1, U1 = syev3.syev3_batched(At, compensated=True, counters=c1)
+    nb = syev3.workspace_bytes(At.shape[0], At.dtype, compensated=True)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        c2 = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device="cuda")
+        lam2, U2 = syev3.syev3_batched(At, compensated=True, counters=c2, workspace=ws)
+        torch.cuda.synchronize()
+        assert torch.equal(c1, c2)
+        assert float((lam1 - lam2).abs().max()) <= 4 * parity.EPS32 * float(lam1.abs().max())
+        lam_o, U_o = oracle.syev3(A.astype(np.float64))
+        vec_gap_filtered_compare(A, lam2.cpu().numpy(), U2.cpu().numpy(), lam_o, U_o)
+    lib = syev3.library()
+    lam3 = torch.empty((At.shape[0], 3), dtype=torch.float32, device="cuda")
+    args = (At.data_ptr(), At.shape[0], lam3.data_ptr(), None, syev3.SYEV3_F32_COMPENSATED, None)
+    assert lib.syev3_batched_ws(*args, ws.data_ptr(), nb - 1, None) == syev3.SYEV3_EINVAL
+    assert lib.syev3_batched_ws(*args, ws.data_ptr() + 16, nb - 256, None) == syev3.SYEV3_EINVAL
+    assert lib.syev3_batched_ws(*args, At.data_ptr(), nb, None) == syev3.SYEV3_EINVAL
+    assert lib.syev3_batched_ws(*args, ws.data_ptr(), nb, None) == syev3.SYEV3_OK
+    torch.cuda.synchronize()
