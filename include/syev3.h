@@ -117,6 +117,28 @@ size_t syev3_workspace_bytes(int64_t n, int dtype);
 int syev3_batched_ws(const void* A_packed6, int64_t n, void* lambda, void* U, int dtype, uint64_t* d_counters,
                      void* d_workspace, size_t workspace_bytes, syev3_stream_t stream);
 
+/* syev3_batched_static_ws -- syev3_batched_ws for SYEV3_F32_COMPENSATED
+ * with the scratch list in the library's static device memory (a file-scope
+ * __device__ array of SYEV3_STATIC_MAX_N records, 12.6 MB), so that the call
+ * allocates nothing and needs no workspace from the caller.  Not in the
+ * paper (which has no counterpart to any of the memory management here):
+ * for callers that cannot pass a workspace -- a C caller without a device
+ * allocator of its own, or code that must not call cudaMalloc/cudaFree on
+ * this path (they synchronise the device and can fail under memory
+ * pressure).
+ *   A_packed6, lambda, U, d_counters, stream: as syev3_batched_ex with
+ *   dtype SYEV3_F32_COMPENSATED (float32 buffers).
+ *   n : 0 <= n <= SYEV3_STATIC_MAX_N, else SYEV3_EINVAL (nothing launched).
+ * The array is shared by every call on a device: calls that overlap in time
+ * (other streams or host threads) race on it and must be ordered by the
+ * caller.  The first call on a device resolves the array's address
+ * (cudaGetSymbolAddress, with that device current); it must come before any
+ * stream capture begins on that device.  Errors as syev3_batched_ws. */
+#define SYEV3_STATIC_MAX_N 262144
+
+int syev3_batched_static_ws(const void* A_packed6, int64_t n, void* lambda, void* U, uint64_t* d_counters,
+                            syev3_stream_t stream);
+
 /* syev3_batched_method -- syev3_batched (FP64 only) with the variants of
  * the method the paper also describes, for studying them against the
  * production path:

@@ -49,6 +49,10 @@ template <class T>
 cudaError_t launch_bwd(const T* lam, const T* U, const T* gl, const T* gU, int64_t n, T* gA, T tau,
                        cudaStream_t stream);
 
+// Record e as this host thread's last CUDA error (syev3_last_cuda_error),
+// clear the runtime's last-error state, and return SYEV3_ECUDA.
+int record_cuda_error(cudaError_t e);
+
 // Read and clear the __device__ status word of each translation unit
 // (synchronise the device).
 cudaError_t take_flags_f64(unsigned* flags);

@@ -58,6 +58,11 @@ int check_forward(const void* A, int64_t n, const void* lam, const void* U, int 
 
 }  // namespace
 
+int syev3::record_cuda_error(cudaError_t e) {
+  cudaGetLastError();
+  return cuda_fail(e);
+}
+
 extern "C" {
 
 int syev3_abi_version(void) { return 1; }

@@ -63,6 +63,8 @@ def _load():
             lib.syev3_workspace_bytes.restype = ctypes.c_size_t
             lib.syev3_batched_ws.argtypes = [vp, i64, vp, vp, i32, vp, vp, ctypes.c_size_t, vp]
             lib.syev3_batched_ws.restype = i32
+            lib.syev3_batched_static_ws.argtypes = [vp, i64, vp, vp, vp, vp]
+            lib.syev3_batched_static_ws.restype = i32
             lib.syev3_batched_bwd.argtypes = [vp, vp, vp, vp, i64, vp, ctypes.c_double, i32, vp]
             lib.syev3_batched_bwd.restype = i32
             lib.syev3_batched_host.argtypes = [vp, i64, vp, vp, i32, i64, vp]
@@ -164,6 +166,31 @@ def syev3_batched_method(A6: torch.Tensor, *, zero_finder: int = ZF_PRODUCTION,
     st = _load().syev3_batched_method(_ptr(A6), n, _ptr(lam), _ptr(U), SYEV3_F64, ctypes.byref(m), _ptr(stats),
                                       _stream(stream))
     _check(st, "syev3_batched_method")
+    return lam, U
+
+
+# Largest batch of syev3_batched_static_ws (its scratch is a static array).
+STATIC_MAX_N = 262144
+
+
+def syev3_batched_static_ws(A6: torch.Tensor, *, vectors: bool = True,
+                            out: tuple[torch.Tensor, torch.Tensor | None] | None = None,
+                            counters: torch.Tensor | None = None, stream=None):
+    """The compensated FP32 solve with its refinement list in the library's
+    static device memory (no workspace, no allocation); n <= STATIC_MAX_N.
+    Calls on one device must not overlap in time."""
+    if not A6.is_cuda or A6.dtype != torch.float32:
+        raise ValueError("A6 must be a float32 CUDA tensor (no CPU fallback)")
+    if A6.dim() != 2 or A6.shape[1] != 6 or not A6.is_contiguous():
+        raise ValueError("A6 must be a contiguous (n, 6) tensor")
+    n = A6.shape[0]
+    if out is None:
+        lam = torch.empty((n, 3), dtype=A6.dtype, device=A6.device)
+        U = torch.empty((n, 3, 3), dtype=A6.dtype, device=A6.device) if vectors else None
+    else:
+        lam, U = out
+    st = _load().syev3_batched_static_ws(_ptr(A6), n, _ptr(lam), _ptr(U), _ptr(counters), _stream(stream))
+    _check(st, "syev3_batched_static_ws")
     return lam, U
 
 
