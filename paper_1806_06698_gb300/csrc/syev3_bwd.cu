@@ -46,11 +46,6 @@ __device__ __forceinline__ float recip<float>(float x) {
   return 1.0f / x;
 }
 
-template <class T>
-__device__ __forceinline__ T sqrtT(T x) {
-  return sqrt(x);
-}
-
 // Packed gradient of one matrix.  l[3] ascending eigenvalues, U[9] row-major
 // with eigenvector columns, gl[3], gU[9] (or has_gU false), tau.
 template <class T>
@@ -69,12 +64,12 @@ __device__ __forceinline__ void grad_one(const T l[3], const T U[9], const T gl[
       d02 = fma(u0, g2, fma(-u2, g0, d02));
       d12 = fma(u1, g2, fma(-u2, g1, d12));
     }
-    const T nrm = sqrtT(fma(l[0], l[0], fma(l[1], l[1], l[2] * l[2])));
-    const T thr = tau * nrm;
+    // |gap| < tau ||lambda||_2, compared squared (no square root).
+    const T thr2 = (tau * tau) * fma(l[0], l[0], fma(l[1], l[1], l[2] * l[2]));
     const T gap01 = l[1] - l[0], gap02 = l[2] - l[0], gap12 = l[2] - l[1];
-    c01 = (fabs(gap01) < thr) ? T(0) : T(0.5) * d01 * recip(gap01);
-    c02 = (fabs(gap02) < thr) ? T(0) : T(0.5) * d02 * recip(gap02);
-    c12 = (fabs(gap12) < thr) ? T(0) : T(0.5) * d12 * recip(gap12);
+    c01 = (gap01 * gap01 < thr2) ? T(0) : T(0.5) * d01 * recip(gap01);
+    c02 = (gap02 * gap02 < thr2) ? T(0) : T(0.5) * d02 * recip(gap02);
+    c12 = (gap12 * gap12 < thr2) ? T(0) : T(0.5) * d12 * recip(gap12);
   }
   const T C[3][3] = {{gl[0], c01, c02}, {c01, gl[1], c12}, {c02, c12, gl[2]}};
   // P = U sym(C); S = P U^T (upper triangle).

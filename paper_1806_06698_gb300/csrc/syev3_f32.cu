@@ -276,11 +276,11 @@ __device__ __forceinline__ void finish32(const Lane32& L, float mu, float nu, fl
     l[1] = (nu - mu) + g;
     l[2] = a2 - nu;
     const float mpa = mu + abar, npa = nu + abar;
-    v[0][0] = b1 * mpa;         v[0][1] = b2 * mu;         v[0][2] = mu * mpa;
-    v[1][0] = -(b2 * mu) * npa; v[1][1] = (b1 * nu) * mpa; v[1][2] = (b1 * b2) * abar;
-    v[2][0] = b1 * nu;          v[2][1] = b2 * npa;        v[2][2] = -(nu * npa);
+    v[0][0] = b1 * mpa; v[0][1] = b2 * mu;  v[0][2] = mu * mpa;
+    v[2][0] = b1 * nu;  v[2][1] = b2 * npa; v[2][2] = -(nu * npa);
+    v[1][0] = v[1][1] = v[1][2] = 0.f;  // u2 = u1 x u3, formed below in the input frame
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 3; k += 2) {
       float ss = fmaf(v[k][0], v[k][0], fmaf(v[k][1], v[k][1], v[k][2] * v[k][2]));
       if (!(ss >= 0x1p-100f)) {  // squares near underflow: exact power-of-two rescale
         int E = 1;
@@ -296,10 +296,22 @@ __device__ __forceinline__ void finish32(const Lane32& L, float mu, float nu, fl
   }
   float x[3][3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 3; k += 2) {
     x[k][0] = fmaf(L.c, v[k][0], -L.s * v[k][1]);
     x[k][1] = fmaf(L.s, v[k][0], L.c * v[k][1]);
     x[k][2] = v[k][2];
+  }
+  if (L.cls == kRed) {
+    // u2 is the cross product of u1 and u3 (Sec. 1.3), of the normalised
+    // vectors and in the input frame ((J u1) x (J u3) = J (u1 x u3)): no
+    // normalisation and no back-transform of its own.
+    x[1][0] = fmaf(x[0][1], x[2][2], -x[0][2] * x[2][1]);
+    x[1][1] = fmaf(x[0][2], x[2][0], -x[0][0] * x[2][2]);
+    x[1][2] = fmaf(x[0][0], x[2][1], -x[0][1] * x[2][0]);
+  } else {
+    x[1][0] = fmaf(L.c, v[1][0], -L.s * v[1][1]);
+    x[1][1] = fmaf(L.s, v[1][0], L.c * v[1][1]);
+    x[1][2] = v[1][2];
   }
   float l0 = l[0], l1 = l[1], l2 = l[2];
   float x00 = x[0][0], x01 = x[0][1], x02 = x[0][2];
