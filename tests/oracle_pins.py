@@ -499,6 +499,36 @@ def eispack_test_is_weaker():
 
 
 @pin
+def deflation_constant_sweep():
+    """The unstated C of the deflation test (Sec. 1.1) swept over 1, 4, 16:
+    deflations only grow with C, and every result stays within the bound the
+    test is built on -- the coupling a deflation drops is at most
+    C eps |alpha1 + alpha2| <= 2 C eps ||A||_F (Wielandt-Hoffman, as Sec. 1.1
+    invokes it), so eigenvalues agree with the double-double brute force to
+    (8 + 2C) eps ||A||_F."""
+    rng = np.random.default_rng(23)
+    n = 3000
+    a1 = rng.standard_normal(n)
+    a2 = a1 - np.abs(a1) * 10.0 ** rng.uniform(-17, -12, n)
+    ang = rng.uniform(0, np.pi / 2, n) * 10.0 ** rng.uniform(-10, 0, n)
+    A = np.concatenate([np.stack([a1, a2, rng.standard_normal(n), np.zeros(n), np.cos(ang), np.sin(ang)], axis=1),
+                        inputs.trace_free_spiked(1000, seed=24)])
+    hi, lo, _ = oracle.dd_jacobi(A)
+    nrm = fro(A)
+    prev = -1
+    for C in (1.0, 4.0, 16.0):
+        lam, U, info = oracle.syev3(A, with_info=True, c_defl=C)
+        ndefl = int((info[:, 0] == oracle.CLS_DEFLATED).sum())
+        assert ndefl >= prev, (C, ndefl, prev)
+        prev = ndefl
+        err = np.max(np.abs((lam - hi) - lo), axis=1) / nrm
+        assert err.max() <= (8 + 2 * C) * EPS, (C, err.max() / EPS)
+        assert np.all(residual(A, lam, U) <= (1e-14 + 2 * C * EPS) * nrm)
+        assert np.all(orthogonality(U) <= 10 * EPS)
+    assert prev > 0
+
+
+@pin
 def iteration_counts():
     """Cubic convergence (Sec. 1.4.1) from the start of Eq. (7): on iid
     N(0,1) matrices the mean is at most 3 steps per root and no root takes
