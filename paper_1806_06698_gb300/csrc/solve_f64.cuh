@@ -186,7 +186,8 @@ __device__ __forceinline__ int finish64(const double ab, const double b1, const 
   double r1 = rcp64(x), r2 = rcp64(x + ab);
   double t1 = b1 * r1, t2 = b2 * r2;
   double f = ((x + lead) - t1) + (small ? c * x * r2 : -t2);
-  const double fp = fma(t2, r2, fma(t1, r1, 1.0));  // Eq. (3)
+  const double t1r = t1 * r1, t2r = t2 * r2;  // b1/x^2, b2/(x+ab)^2
+  const double fp = (1.0 + t1r) + t2r;        // Eq. (3)
   if (!is_pos(f)) return 2;
   // The step of Eqs. (5), (6): Delta = (f/b) S(z) with b = f' + f/x,
   // z = -4 omega_0 f / (x b^2) and S(z) = 2/(1 + sqrt(1 + z)).  Only f/b is
@@ -209,6 +210,24 @@ __device__ __forceinline__ int finish64(const double ab, const double b1, const 
   if (dbits(delta) >= dbits(x) - (1ull << 52)) return 1;
   const double xn = x - delta;
   if (!(dbits(xn) < dbits(x))) return 0;  // the step no longer moves x: rounding level
+  if (dbits(delta) <= dbits(x) - (16ull << 52)) {
+    // delta <= 2^-16 x (every step from an FP32 start in practice): f at
+    // the new iterate from Taylor's formula about x to third order,
+    //   f(xn) = f - delta f1 + delta^2 f2/2 - delta^3 f3/6 + delta^4 f4(xi)/24,
+    // with f1 = f', f2 = -2 (b1/x^3 + b2/(x+ab)^3), f3 = 6 (b1/x^4 +
+    // b2/(x+ab)^4) and |f4| <= 24 f1/x^3 (1 + 2^-13) on [xn, x]: the dropped
+    // term is below 2^-64 x f1, far under the stopping threshold, and the
+    // rounding error of this form is that of f itself (the leading terms
+    // cancel to the size of the next).  The threshold uses f1(x) <= f1(xn):
+    // at most 2^-15 stricter.
+    const double s1 = t1r * r1, s2 = t2r * r2;  // b1/x^3, b2/(x+ab)^3
+    const double hc = fma(s1, fma(delta, r1, 1.0), s2 * fma(delta, r2, 1.0));
+    const double fn = fma(-(delta * delta), hc, fma(-delta, fp, f));
+    x = xn;
+    if (!is_pos(fn)) return 0;  // at or past the root: rounding level
+    if (dbits(fn) < dbits(x * fp) - (51ull << 52)) return 0;  // f/f1 < 2^-51 x (Sec. 1.4.1)
+    return 1;
+  }
   x = xn;
   r1 = rcp64(x);
   r2 = rcp64(x + ab);
