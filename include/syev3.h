@@ -209,7 +209,7 @@ int syev3_batched_bwd(const void* lambda, const void* U, const void* g_lambda, c
 
 /* syev3_batched_host -- syev3_batched for buffers in host memory
  * (blocking).  The batch is cut into chunks of `chunk` matrices (<= 0:
- * 2^19); each chunk is copied in, solved and copied out on one of three
+ * 2^20); each chunk is copied in, solved and copied out on one of three
  * library streams, so copies overlap the solves of neighbouring chunks.
  *   A_host      : host, n x 6 of dtype (page-locked memory lets the copies
  *                 run asynchronously; pageable memory works, slower).

@@ -45,7 +45,7 @@ int syev3_batched_host(const void* A_host, int64_t n, void* lambda_host, void* U
   if (n < 0 || (dtype != SYEV3_F64 && dtype != SYEV3_F32 && dtype != SYEV3_F32_COMPENSATED)) return SYEV3_EINVAL;
   if (n == 0) return SYEV3_OK;
   if (A_host == nullptr || lambda_host == nullptr) return SYEV3_EINVAL;
-  if (chunk <= 0) chunk = (int64_t)1 << 19;  // measured: copy-bound, 2^19 fills and drains the pipeline fastest
+  if (chunk <= 0) chunk = (int64_t)1 << 20;  // measured: copy-bound; 2^20 was fastest and steadiest
   const size_t es = dtype == SYEV3_F64 ? 8 : 4;
   const size_t in_b = 6 * es, lam_b = 3 * es, U_b = 9 * es;
   const size_t lam_off = (size_t)chunk * in_b, U_off = lam_off + ((size_t)chunk * lam_b + 255) / 256 * 256;

@@ -232,3 +232,33 @@ def test_workspace_path_matches_single_kernel(syev3):
     assert lib.syev3_batched_ws(*args, At.data_ptr(), nb, None) == syev3.SYEV3_EINVAL
     assert lib.syev3_batched_ws(*args, ws.data_ptr(), nb, None) == syev3.SYEV3_OK
     torch.cuda.synchronize()
+
+
+def test_batch_beyond_32_bit_element_indices(syev3):
+    """n = 2^29 FP32 matrices (eigenvector elements up to 4.8e9 > 2^32): the
+    kernels' 64-bit index arithmetic.  Inputs are generated on the device;
+    every output is checked for ordering, orthogonality and the trace, and
+    sampled matrices at the far end against the oracle."""
+    n = 1 << 29
+    free, _ = torch.cuda.mem_get_info()
+    if free < 48 << 30:
+        pytest.skip("needs about 48 GB of free device memory")
+    g = torch.Generator(device="cuda").manual_seed(5)
+    A = torch.randn((n, 6), device="cuda", dtype=torch.float32, generator=g)
+    lam, U = syev3.syev3_batched(A)
+    torch.cuda.synchronize()
+    step = 1 << 25
+    for b in range(0, n, step):
+        l, u, a = lam[b:b + step], U[b:b + step], A[b:b + step]
+        assert bool(torch.all(l[:, 1:] >= l[:, :-1]))
+        orth = torch.linalg.matrix_norm(u.transpose(1, 2) @ u - torch.eye(3, device="cuda"))
+        assert float(orth.max()) <= 64 * parity.EPS32
+        tr = a[:, 0].double() + a[:, 1].double() + a[:, 2].double()
+        nrm = torch.linalg.vector_norm(a.double(), dim=1)
+        assert float(((l.double().sum(dim=1) - tr).abs() / nrm).max()) <= 64 * parity.EPS32
+    idx = torch.arange(n - 4096, n, device="cuda")
+    As = A[idx].cpu().numpy()
+    lam_o, U_o = oracle.syev3(As.astype(np.float64))
+    vec_gap_filtered_compare(As, lam[idx].cpu().numpy(), U[idx].cpu().numpy(), lam_o, U_o)
+    del A, lam, U
+    torch.cuda.empty_cache()
