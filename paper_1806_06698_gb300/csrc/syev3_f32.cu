@@ -193,10 +193,12 @@ __device__ __forceinline__ float bg_step32(const float ab, const float b1, const
 // mu and nu in FP32 on a fixed schedule: from the start of f64::start32 two
 // Borges-Gragg steps for both problems, straight-line (no lane leaves
 // early, so the warp stays converged).  From these starts two steps reach
-// FP32 accuracy for most problems (cubic convergence); more[k] marks a
-// problem whose second step still moved x by more than 2^-16 x, or whose
-// small-root start turned out left of the root: the kernel finishes those
-// on a compacted work list with roots32_more.
+// FP32 accuracy for most problems: the second step moves x by about the
+// error the first one left, and the step converges cubically, so a move
+// below 2^-12 x leaves an error of order 2^-36 x.  more[k] marks a problem
+// whose second step moved x by more than that, or whose small-root start
+// turned out left of the root: the kernel finishes those on a compacted
+// work list with roots32_more.
 __device__ __forceinline__ void roots32(const float ab, const float b1[2], const float b2[2], const float g[2],
                                         const float c[2], const float K[2], float x[2], bool more[2]) {
 #pragma unroll
@@ -208,7 +210,7 @@ __device__ __forceinline__ void roots32(const float ab, const float b1[2], const
     const bool restart = model && !(f0 > 0.f);  // the small-root start was not right of the root
     if (restart) x1 = x7;
     const float x2 = bg_step32(ab, b1[k], b2[k], g[k], c[k], K[k], x1, &f1);
-    more[k] = restart || (x1 - x2) > 0x1p-16f * x2;
+    more[k] = restart || (x1 - x2) > 0x1p-12f * x2;
     x[k] = x2;
   }
 }
