@@ -620,6 +620,20 @@ def run_native(args):
     e2e_ms = max_over_ranks(e2e_ms, dev)
     e2e_value = whole_job_rate(n, ws, e2e_steps, e2e_ms)
 
+    # Eigenvalues only (U = NULL): the same batch, no eigenvectors formed or
+    # written (24 B out per matrix).
+    lam_only = torch.empty((n, 3), dtype=torch.float64, device=dev)
+
+    def values_step():
+        syev3.syev3_batched(A, out=(lam_only, None), stream=stream)
+
+    v_ms, v_kms = _timed(values_step, min(args.steps, 20), args.warmup, stream, barrier)
+    v_rate = n * min(args.steps, 20) / (v_ms * 1e-3)
+    values_only = {"value": v_rate, "unit": UNIT, "ms_per_step": v_ms / min(args.steps, 20),
+                   "bytes_per_matrix": 72, "hbm_frac_of_measured": 72 * v_rate / 1e9 /
+                   load_peaks().get("hbm_gbs", 6686.1), "kernel": "k_syev3_f64<bulk, production, values only>"}
+    del lam_only
+
     fp32 = None if args.fp64_only else _fp32_legs(args, dev, stream, barrier, A)
     bwd = None if args.fp64_only else _bwd_legs(args, dev, stream, barrier)
     serving = None if (args.fp64_only or args.serve_seconds <= 0) else _serving_leg(args, dev, A)
@@ -652,6 +666,7 @@ def run_native(args):
                     "3-stream copy/solve pipeline, chunks of 2^20)"},
             "clocks": clocks,
         }
+        line["eigenvalues_only"] = values_only
         if fp32 is not None:
             line["precision_form"] = fp32
         if bwd is not None:

@@ -422,6 +422,34 @@ __device__ __forceinline__ Lane make_lane(const double a_in[6]) {
   return L;
 }
 
+// Phase E for eigenvalues only: the values of finish_lane (the same
+// expressions, the same compare-and-swap order and tie rule), unscaled.
+__device__ __forceinline__ void finish_values(const Lane& L, double mu, double nu, double lam[3]) {
+  const double a1 = L.a1, a2 = L.a2, b1 = L.b1, b2 = L.b2, g = L.g;
+  double l0, l1, l2;
+  if (L.cls == kDiagonal) {
+    l0 = a1; l1 = a2; l2 = g;
+  } else if (L.cls == kDeflated) {
+    const double h2 = fma(b1, b1, b2 * b2);
+    const double rh = rsqrt(h2), h = h2 * rh;
+    const double gs = b1 * rh, gc = b2 * rh;
+    l0 = fma(a1 * gc, gc, a2 * gs * gs);
+    const Rot K = ordered_rotation(fma(a1 * gs, gs, a2 * gc * gc), h, g);
+    l1 = K.l1; l2 = K.l2;
+  } else {
+    l0 = a1 + mu;
+    l1 = (nu - mu) + g;
+    l2 = a2 - nu;
+  }
+  double t;
+  if (l1 < l0) { t = l0; l0 = l1; l1 = t; }
+  if (l2 < l1) { t = l1; l1 = l2; l2 = t; }
+  if (l1 < l0) { t = l0; l0 = l1; l1 = t; }
+  lam[0] = mul_pow2(l0, L.e);
+  lam[1] = mul_pow2(l1, L.e);
+  lam[2] = mul_pow2(l2, L.e);
+}
+
 // Phase E: eigenpairs in the arrow frame, back-transform, sort, sign,
 // unscale; writes lam[3] and U[9] (U[i*3+k] = component i of vector k).
 __device__ __forceinline__ void finish_lane(const Lane& L, double mu, double nu, double lam[3], double U[9]) {

@@ -44,7 +44,9 @@ __device__ unsigned g_flags;     // kFlagWaitTimeout when a bulk-copy wait ran o
 // `counters` receives the 8 method statistics (MethodStat) instead of the
 // 4 counters of syev3_batched_ex.  The production build (kStudy = false)
 // has these switches compiled out.
-template <bool kBulkIn, bool kStudy>
+// kVectors = false: eigenvalues only (U_out is NULL); the eigenvectors are
+// not formed.
+template <bool kBulkIn, bool kStudy, bool kVectors>
 __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A, int64_t n,
                                                     double* __restrict__ lam_out, double* __restrict__ U_out,
                                                     unsigned long long* __restrict__ counters, Method method) {
@@ -331,7 +333,18 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
     // belongs to this tile, written straight to memory when carried in), then
     // of one of this tile's other matrices (re-reduced from its record, which
     // is still in shared memory).
-    if (reduced) {
+    if (reduced && !kVectors) {
+      double lam[3];
+      finish_values(L, root[0], root[1], lam);
+      const int64_t row = gidx - base;
+      if (row >= 0 && row < cnt) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s_lam[row * 3 + k] = lam[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) lam_out[gidx * 3 + k] = lam[k];
+      }
+    } else if (reduced) {
       double lam[3], U[9];
       finish_lane(L, root[0], root[1], lam, U);
       const int64_t row = gidx - base;
@@ -361,13 +374,17 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
         for (int k = 0; k < 3; ++k) lam[k] = qnan;
 #pragma unroll
         for (int k = 0; k < 9; ++k) U[k] = qnan;
-      } else {
+      } else if (kVectors) {
         finish_lane(O, 0.0, 0.0, lam, U);
+      } else {
+        finish_values(O, 0.0, 0.0, lam);
       }
 #pragma unroll
       for (int k = 0; k < 3; ++k) s_lam[row * 3 + k] = lam[k];
+      if (kVectors) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) s_U[row * 9 + k] = U[k];
+        for (int k = 0; k < 9; ++k) s_U[row * 9 + k] = U[k];
+      }
     }
     if (counters != nullptr) {
       const unsigned cm = __ballot_sync(0xffffffffu, capped);
@@ -416,18 +433,19 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
   }
 }
 
-template <bool kBulkIn, bool kStudy>
+template <bool kBulkIn, bool kStudy, bool kVectors>
 int blocks_per_sm_f64() {
   static int cached = -1;
   if (cached < 0) {
     int v = 0;
-    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_syev3_f64<kBulkIn, kStudy>, kTPB, 0);
+    const cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_syev3_f64<kBulkIn, kStudy, kVectors>, kTPB, 0);
     cached = (e == cudaSuccess && v > 0) ? v : 1;
   }
   return cached;
 }
 
-template <bool kBulkIn, bool kStudy>
+template <bool kBulkIn, bool kStudy, bool kVectors = true>
 cudaError_t launch_f64_t(const double* A, int64_t n, double* lam, double* U, unsigned long long* counters,
                          Method method, cudaStream_t stream) {
   int dev = 0, sms = 0;
@@ -436,9 +454,9 @@ cudaError_t launch_f64_t(const double* A, int64_t n, double* lam, double* U, uns
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const int64_t n_tiles = (n + kTPB - 1) / kTPB;
-  const int64_t resident = (int64_t)sms * blocks_per_sm_f64<kBulkIn, kStudy>();
+  const int64_t resident = (int64_t)sms * blocks_per_sm_f64<kBulkIn, kStudy, kVectors>();
   const int grid = (int)(n_tiles < resident ? n_tiles : resident);
-  k_syev3_f64<kBulkIn, kStudy><<<grid, kTPB, 0, stream>>>(A, n, lam, U, counters, method);
+  k_syev3_f64<kBulkIn, kStudy, kVectors><<<grid, kTPB, 0, stream>>>(A, n, lam, U, counters, method);
   return cudaGetLastError();
 }
 
@@ -448,7 +466,10 @@ cudaError_t launch_f64(const double* A, int64_t n, double* lam, double* U, unsig
                        cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const Method m{kZfProduction, kDeflSimplified};
-  if ((reinterpret_cast<uintptr_t>(A) & 15) == 0) return launch_f64_t<true, false>(A, n, lam, U, counters, m, stream);
+  if ((reinterpret_cast<uintptr_t>(A) & 15) == 0) {
+    if (U == nullptr) return launch_f64_t<true, false, false>(A, n, lam, U, counters, m, stream);
+    return launch_f64_t<true, false>(A, n, lam, U, counters, m, stream);
+  }
   return launch_f64_t<false, false>(A, n, lam, U, counters, m, stream);
 }
 

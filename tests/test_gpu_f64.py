@@ -62,8 +62,12 @@ def test_mixed_subsets_and_exact_diagonals(syev3):
     assert np.array_equal(lam[d], lam_o[d]) and np.array_equal(U[d], U_o[d])
 
 
-def test_eigenvalues_only_matches(syev3):
-    A, _ = inputs.mixed(5000, seed=78)
+@pytest.mark.parametrize("n", [1, 129, 5000, 20011])
+def test_eigenvalues_only_matches(syev3, n):
+    """The eigenvalues-only kernel (no eigenvectors formed) returns the
+    eigenvalues of the full solve bit for bit, at sizes that exercise the
+    carried arrows and the final pass."""
+    A, _ = inputs.mixed(n, seed=78 + n)
     lam_v, _ = run_gpu(syev3, A, vectors=True)
     lam_n, U_n = run_gpu(syev3, A, vectors=False)
     assert U_n is None
