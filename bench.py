@@ -327,7 +327,21 @@ def _fp32_legs(args, dev, stream, barrier, A64_dev):
                 "max_orthogonality_eps32": orth / 2.0 ** -23,
                 "accuracy_sample": int(idx.numel()),
             }
-        del A, lam, U, A_ref, ws
+        # Eigenvalues only (plain FP32, U = NULL): 24 B in + 12 B out.
+        lam_v = torch.empty((n, 3), dtype=torch.float32, device=dev)
+
+        def vstep():
+            syev3.syev3_batched(A, out=(lam_v, None), stream=stream)
+
+        v_ms, v_kms = _timed(vstep, args.steps, args.warmup, stream, barrier)
+        k = statistics.mean(v_kms)
+        gbs = 36 * n / (k * 1e-3) / 1e9
+        out[f"{name}_plain_eigenvalues_only"] = {
+            "value": n * args.steps / (v_ms * 1e-3), "unit": UNIT, "ms_per_step": v_ms / args.steps, "dtype": "f32",
+            "n": n, "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                                 "traffic": None, "kernel": "k_syev3_f32<plain, values only>",
+                                 "peak_source": "MEASURED_PEAKS hbm_gbs"}}
+        del A, lam, U, A_ref, ws, lam_v
         torch.cuda.empty_cache()
     return out
 

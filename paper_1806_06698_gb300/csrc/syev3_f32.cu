@@ -252,6 +252,32 @@ __device__ __forceinline__ float newton_ff(const F2 ab, const F2 b1, const F2 b2
 
 // Eigenpairs of a classified lane in FP32 (scaled frame); returns eigenvalues
 // ascending in l[] and vectors as columns in U[i*3+k].
+// Eigenvalues only: those of finish32 (the same expressions, compare order
+// and tie rule), ascending, in the scaled frame.
+__device__ __forceinline__ void finish32_values(const Lane32& L, float mu, float nu, float l_out[3]) {
+  const float a1 = L.a1, a2 = L.a2, b1 = L.b1, b2 = L.b2, g = L.g;
+  float l0, l1, l2;
+  if (L.cls == kDiag) {
+    l0 = a1; l1 = a2; l2 = g;
+  } else if (L.cls == kDefl) {
+    const float h2 = fmaf(b1, b1, b2 * b2);
+    const float rh = rsqrt32(h2), h = h2 * rh;
+    const float gs = b1 * rh, gc = b2 * rh;
+    l0 = fmaf(a1 * gc, gc, a2 * gs * gs);
+    const Rot32 K = ordered_rotation32(fmaf(a1 * gs, gs, a2 * gc * gc), h, g);
+    l1 = K.l1; l2 = K.l2;
+  } else {
+    l0 = a1 + mu;
+    l1 = (nu - mu) + g;
+    l2 = a2 - nu;
+  }
+  float t;
+  if (l1 < l0) { t = l0; l0 = l1; l1 = t; }
+  if (l2 < l1) { t = l1; l1 = l2; l2 = t; }
+  if (l1 < l0) { t = l0; l0 = l1; l1 = t; }
+  l_out[0] = l0; l_out[1] = l1; l_out[2] = l2;
+}
+
 __device__ __forceinline__ void finish32(const Lane32& L, float mu, float nu, float l_out[3], float U[9]) {
   const float a1 = L.a1, a2 = L.a2, b1 = L.b1, b2 = L.b2, g = L.g;
   float l[3], v[3][3];
@@ -398,7 +424,8 @@ __device__ __forceinline__ bool refine_one(const float f[9], const int code, con
 // flagged lanes appended to a list in global memory -- the workspace of
 // syev3_batched_ws -- and refined by k_refine_f32; the kernel then holds no
 // FP64 code and needs fewer registers).
-template <bool kBulkIn, int kMode>
+// kVectors = false (plain mode only): eigenvalues only, U_out NULL.
+template <bool kBulkIn, int kMode, bool kVectors = true>
 __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A, int64_t n,
                                                     float* __restrict__ lam_out, float* __restrict__ U_out,
                                                     unsigned long long* __restrict__ counters,
@@ -562,6 +589,10 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
         for (int k = 0; k < 3; ++k) l[k] = qnan;
 #pragma unroll
         for (int k = 0; k < 9; ++k) U[k] = qnan;
+      } else if (!kVectors) {
+        finish32_values(L, root[0], root[1], l);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) l[k] = unscale32(l[k], L.e);
       } else {
         finish32(L, root[0], root[1], l, U);
         if (kComp && L.cls != kDiag) {
@@ -574,8 +605,10 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
       }
 #pragma unroll
       for (int k = 0; k < 3; ++k) s_lam[tid * 3 + k] = l[k];
+      if (kVectors) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) s_U[tid * 9 + k] = U[k];
+        for (int k = 0; k < 9; ++k) s_U[tid * 9 + k] = U[k];
+      }
     }
 
     if (kDefer) {
@@ -667,24 +700,24 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
   }
 }
 
-template <bool kBulkIn, int kMode>
+template <bool kBulkIn, int kMode, bool kVectors>
 int blocks_per_sm_f32() {
   static int cached = -1;
   if (cached < 0) {
     int v = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_syev3_f32<kBulkIn, kMode>, kTPB, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_syev3_f32<kBulkIn, kMode, kVectors>, kTPB, 0);
     cached = (e == cudaSuccess && v > 0) ? v : 1;
   }
   return cached;
 }
 
-template <bool kBulkIn, int kMode>
+template <bool kBulkIn, int kMode, bool kVectors = true>
 cudaError_t launch(const float* A, int64_t n, float* lam, float* U, unsigned long long* counters,
                    FlagRec* flag_list, unsigned long long* flag_count, cudaStream_t stream, int sms) {
   const int64_t n_tiles = (n + kTPB - 1) / kTPB;
-  const int64_t resident = (int64_t)sms * blocks_per_sm_f32<kBulkIn, kMode>();
+  const int64_t resident = (int64_t)sms * blocks_per_sm_f32<kBulkIn, kMode, kVectors>();
   const int grid = (int)(n_tiles < resident ? n_tiles : resident);
-  k_syev3_f32<kBulkIn, kMode><<<grid, kTPB, 0, stream>>>(A, n, lam, U, counters, flag_list, flag_count);
+  k_syev3_f32<kBulkIn, kMode, kVectors><<<grid, kTPB, 0, stream>>>(A, n, lam, U, counters, flag_list, flag_count);
   return cudaGetLastError();
 }
 
@@ -734,6 +767,8 @@ cudaError_t launch_f32(const float* A, int64_t n, float* lam, float* U, bool com
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const bool bulk = (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+  if (bulk && !compensated && U == nullptr)
+    return launch<true, kPlain, false>(A, n, lam, U, counters, nullptr, nullptr, stream, sms);
   if (bulk)
     return compensated ? launch<true, kInline>(A, n, lam, U, counters, nullptr, nullptr, stream, sms)
                        : launch<true, kPlain>(A, n, lam, U, counters, nullptr, nullptr, stream, sms);
