@@ -224,8 +224,17 @@ int syev3_batched_host(const void* A_host, int64_t n, void* lambda_host, void* U
 
 /* Device-side status bits of the current device, OR-ed over all launches
  * since the last call, then cleared (synchronises the device).
- *   bit 0: a bulk-copy wait timed out (SYEV3_ETIMEOUT). */
+ *   bit 0: a bulk-copy wait timed out (SYEV3_ETIMEOUT).  Every wait of the
+ *   kernels on a bulk copy is bounded (1 s of the GPU's global timer); a CTA
+ *   whose wait runs out records this bit, lets its copies in flight land and
+ *   exits, so the context stays usable. */
 int syev3_device_flags(uint32_t* flags);
+
+/* syev3_selftest_wait_limit -- exercises that failure path: launches one CTA
+ * that waits on an mbarrier nothing completes; after the wait limit (about
+ * 1 s) it sets bit 0 of the device flags and exits.  For tests of the
+ * failure handling; not in the paper.  Asynchronous on `stream`. */
+int syev3_selftest_wait_limit(syev3_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Serving: a continuous-batching request server (not in the paper).

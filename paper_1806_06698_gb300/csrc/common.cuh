@@ -12,10 +12,20 @@ namespace syev3 {
 // Device status bits (OR-ed into a per-translation-unit __device__ word).
 constexpr unsigned kFlagWaitTimeout = 1u;
 
-// Polls of an mbarrier before a wait is declared lost.  A 12 KB bulk copy
-// lands in microseconds; 1 << 22 polls with the suspend hint below is well
-// over a second.
+// Limit of a wait on an mbarrier, on the GPU's global nanosecond timer: a
+// 12 KB bulk copy lands in microseconds, so a wait still open after a second
+// is declared lost.  Each poll may suspend the thread for up to
+// kSuspendHintNs; kMaxPolls is a backstop should the timer not advance
+// (at most kMaxPolls x kSuspendHintNs = 84 s).
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+constexpr uint32_t kSuspendHintNs = 20000u;
 constexpr uint32_t kMaxPolls = 1u << 22;
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -36,9 +46,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 }
 
 // Returns true once the phase with the given parity has completed, false if
-// kMaxPolls polls went by first.
+// kWaitLimitNs went by first (timed from the first poll that found the phase
+// open; the normal path reads no timer).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t addr = smem_u32(bar);
+  uint64_t t0 = 0;
   for (uint32_t i = 0; i < kMaxPolls; ++i) {
     uint32_t done;
     asm volatile(
@@ -46,9 +58,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(addr), "r"(parity), "r"(1000000u)
+        : "r"(addr), "r"(parity), "r"(kSuspendHintNs)
         : "memory");
     if (done) return true;
+    if (i == 0)
+      t0 = global_ns();
+    else if (global_ns() - t0 > kWaitLimitNs)
+      return false;
   }
   return false;
 }

@@ -49,6 +49,9 @@ template <class T>
 cudaError_t launch_bwd(const T* lam, const T* U, const T* gl, const T* gU, int64_t n, T* gA, T tau,
                        cudaStream_t stream);
 
+// One CTA whose bounded wait runs out (syev3_selftest_wait_limit).
+cudaError_t launch_wait_selftest(cudaStream_t stream);
+
 // Record e as this host thread's last CUDA error (syev3_last_cuda_error),
 // clear the runtime's last-error state, and return SYEV3_ECUDA.
 int record_cuda_error(cudaError_t e);

@@ -181,6 +181,11 @@ int syev3_batched_bwd(const void* lambda, const void* U, const void* g_lambda, c
   return e == cudaSuccess ? SYEV3_OK : cuda_fail(e);
 }
 
+int syev3_selftest_wait_limit(syev3_stream_t stream) {
+  const cudaError_t e = syev3::launch_wait_selftest(reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SYEV3_OK : cuda_fail(e);
+}
+
 int syev3_device_flags(uint32_t* flags) {
   if (flags == nullptr) return SYEV3_EINVAL;
   cudaError_t e = cudaDeviceSynchronize();

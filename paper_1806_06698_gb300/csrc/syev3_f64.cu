@@ -481,6 +481,23 @@ cudaError_t launch_f64_method(const double* A, int64_t n, double* lam, double* U
   return launch_f64_t<false, true>(A, n, lam, U, stats, method, stream);
 }
 
+// The failure path of the bounded waits, exercised: one thread waits on an
+// mbarrier that nothing completes (no copy is issued, nothing arrives), so
+// the wait runs out after kWaitLimitNs and the timeout bit is recorded, as a
+// lost bulk copy would record it.
+__global__ void k_wait_selftest() {
+  __shared__ alignas(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    if (!mbar_wait(&bar, 0)) atomicOr(&g_flags, kFlagWaitTimeout);
+  }
+}
+
+cudaError_t launch_wait_selftest(cudaStream_t stream) {
+  k_wait_selftest<<<1, 32, 0, stream>>>();
+  return cudaGetLastError();
+}
+
 cudaError_t take_flags_f64(unsigned* flags) {
   unsigned v = 0, zero = 0;
   cudaError_t e = cudaMemcpyFromSymbol(&v, g_flags, sizeof(v));

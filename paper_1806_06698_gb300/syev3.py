@@ -69,6 +69,8 @@ def _load():
             lib.syev3_batched_bwd.restype = i32
             lib.syev3_batched_host.argtypes = [vp, i64, vp, vp, i32, i64, vp]
             lib.syev3_batched_host.restype = i32
+            lib.syev3_selftest_wait_limit.argtypes = [vp]
+            lib.syev3_selftest_wait_limit.restype = i32
             lib.syev3_device_flags.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
             lib.syev3_device_flags.restype = i32
             _lib = lib
