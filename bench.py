@@ -201,18 +201,40 @@ def load_peaks():
         return {}
 
 
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(A: np.ndarray, sample: int, seconds_hint: float = 0.0) -> dict:
     """The CPU FP64 oracle (as it stands) over all host cores on a bounded
-    sample of the workload."""
+    sample of the workload, repeated up to about 10 core-seconds of work;
+    also its single-thread rate on 2^20 matrices of the same batch."""
     import oracle
 
     oracle.build()
     cores = os.cpu_count() or 1
     sub = np.ascontiguousarray(A[:sample])
-    _, _, secs = oracle.syev3_timed(sub, cores)
-    return {"value": sample / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {sample} matrices of the mixed FP64 batch, std::thread over {cores} cores, "
-                      f"{secs:.2f} s wall ({secs * cores:.1f} core-s)"}
+    total, reps = 0.0, 0
+    while reps < 6 and (reps == 0 or total * cores < 10.0):
+        _, _, secs = oracle.syev3_timed(sub, cores)
+        total += secs
+        reps += 1
+    one = np.ascontiguousarray(A[:min(sample, 1 << 20)])
+    _, _, secs1 = oracle.syev3_timed(one, 1)
+    return {"value": sample * reps / total, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} matrices of the mixed FP64 batch x {reps}, std::thread over {cores} "
+                      f"cores, {total:.2f} s wall ({total * cores:.1f} core-s)",
+            "single_thread_value": one.shape[0] / secs1, "single_thread_sample": f"first {one.shape[0]} matrices",
+            "cpu_model": _cpu_model()}
 
 
 def run_reference(args):
