@@ -238,3 +238,32 @@ def test_host_entry_point(syev3, dtype):
     lam0 = torch.empty((n, 3), dtype=At.dtype)
     syev3.syev3_batched_host(At, lam0, None, compensated=comp)
     assert torch.equal(lam0, lam_d.cpu())
+
+
+def test_extreme_magnitudes(syev3):
+    """The pre-scale and unscale fallbacks (scalbn): largest entries at or
+    above 2^1022, wholly subnormal matrices (outputs subnormal), and single
+    subnormal entries among normal ones.  Scaling by 2^k commutes with the
+    solve, so the first two are compared bit for bit with the scaled results
+    of the same matrices at unit scale."""
+    rng = np.random.default_rng(903)
+    A = rng.standard_normal((4000, 6))
+    A *= (0.5 + 0.15 * rng.random(4000))[:, None] / np.max(np.abs(A), axis=1, keepdims=True)  # max in [0.5, 0.65)
+    lam1, U1 = run_gpu(syev3, A)
+    # largest entry in [2^1022, 0.65 * 2^1023): eigenvalues (<= 3 max) stay finite
+    lam, U = run_gpu(syev3, np.ldexp(A, 1023))
+    assert np.all(np.isfinite(lam))
+    assert np.array_equal(lam, np.ldexp(lam1, 1023)) and np.array_equal(U, U1)
+    # wholly subnormal input: compare with the unit-scale solve of the same
+    # (exactly representable) matrices, scaled once
+    As = np.ldexp(A, -1040)
+    Ab = np.ldexp(As, 1040)
+    lam2, U2 = run_gpu(syev3, Ab)
+    lam, U = run_gpu(syev3, As)
+    assert np.array_equal(lam, np.ldexp(lam2, -1040)) and np.array_equal(U, U2)
+    # one subnormal entry in an otherwise normal matrix
+    B = inputs.gaussian(4000, seed=904)
+    B[np.arange(4000), rng.integers(0, 6, 4000)] = np.ldexp(rng.standard_normal(4000), -1060)
+    lam, U = run_gpu(syev3, B)
+    lam_o, U_o = oracle.syev3(B)
+    parity.compare_f64(B, lam, U, lam_o, U_o)
