@@ -713,7 +713,7 @@ def run_native(args):
             line["method_study"] = study
         if accuracy is not None:
             line["accuracy_experiment"] = accuracy
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and ws == 1:  # the host-core baseline: rank 0 at N = 1 only
             line["cpu_baseline"] = cpu_baseline(A_np, n)
         print(json.dumps(line), flush=True)
     if ws > 1:
