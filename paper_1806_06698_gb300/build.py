@@ -8,6 +8,8 @@ Usage: ``python -m paper_1806_06698_gb300.build [--force]``.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import contextlib
+import fcntl
 import glob
 import os
 import shutil
@@ -45,11 +47,30 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
+@contextlib.contextmanager
+def _build_lock():
+    """One build at a time across processes (several ranks of a multi-GPU
+    run may call build() together; they share the object files)."""
+    os.makedirs(OBJ, exist_ok=True)
+    with open(os.path.join(OBJ, ".lock"), "w") as fh:
+        fcntl.flock(fh, fcntl.LOCK_EX)
+        try:
+            yield
+        finally:
+            fcntl.flock(fh, fcntl.LOCK_UN)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
+    with _build_lock():
+        if not force and up_to_date():  # built by another process meanwhile
+            return LIB
+        return _build(verbose)
+
+
+def _build(verbose: bool) -> str:
     nvcc = _nvcc()
-    os.makedirs(OBJ, exist_ok=True)
 
     def compile_one(src: str) -> str:
         obj = os.path.join(OBJ, os.path.basename(src) + ".o")
