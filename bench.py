@@ -699,7 +699,7 @@ def run_native(args):
             "gpu_launches": args.steps,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 48,
                     "d2h_bytes_per_step": n * 96, "api": "syev3_batched_host (pinned host buffers, "
-                    "3-stream copy/solve pipeline, chunks of 2^20)"},
+                    "3-stream copy/solve pipeline, chunks of 2^16 growing by a quarter to 2^20)"},
             "clocks": clocks,
         }
         line["eigenvalues_only"] = values_only

@@ -208,14 +208,16 @@ int syev3_batched_bwd(const void* lambda, const void* U, const void* g_lambda, c
                       void* g_A_packed6, double gap_tau, int dtype, syev3_stream_t stream);
 
 /* syev3_batched_host -- syev3_batched for buffers in host memory
- * (blocking).  The batch is cut into chunks of `chunk` matrices (<= 0:
- * 2^20); each chunk is copied in, solved and copied out on one of three
- * library streams, so copies overlap the solves of neighbouring chunks.
+ * (blocking).  The batch is cut into chunks of `chunk` matrices; with
+ * chunk <= 0 the library's schedule, 2^16 matrices first and each next
+ * chunk a quarter longer up to 2^20 (the first results start back early).
+ * Each chunk is copied in, solved and copied out on one of three library
+ * streams, so copies overlap the solves of neighbouring chunks.
  *   A_host      : host, n x 6 of dtype (page-locked memory lets the copies
  *                 run asynchronously; pageable memory works, slower).
  *   lambda_host : host, n x 3, written.  U_host: host, n x 9, or NULL.
  *   stream      : the pipeline starts after the work queued on it.
- * Device staging buffers (3 x chunk records) are allocated by the library
+ * Device staging buffers (3 x the largest chunk) are allocated by the library
  * on the first call for a device and kept for later calls; they grow when
  * a larger chunk is asked for.  Calls for the same device from several host
  * threads are serialised.  Returns when the host outputs are written. */

@@ -200,7 +200,8 @@ def syev3_batched_host(A6: torch.Tensor, lam: torch.Tensor, U: torch.Tensor | No
                        compensated: bool = False, chunk: int = 0, stream=None):
     """Blocking solve of host (CPU, ideally pinned) tensors through the C
     ABI's pipelined host entry point; fills lam (n,3) and U (n,3,3).
-    ``chunk`` <= 0 takes the library's default (2^20 matrices)."""
+    ``chunk`` <= 0 takes the library's schedule (2^16 matrices first, each
+    next chunk a quarter longer, up to 2^20)."""
     for t in (A6, lam) + ((U,) if U is not None else ()):
         if t.is_cuda or not t.is_contiguous():
             raise ValueError("host buffers must be contiguous CPU tensors")

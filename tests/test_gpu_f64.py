@@ -240,6 +240,23 @@ def test_host_entry_point(syev3, dtype):
     assert torch.equal(lam0, lam_d.cpu())
 
 
+def test_host_entry_point_default_schedule(syev3):
+    """The host entry point's default chunk schedule (2^16 matrices first,
+    each next chunk a quarter longer, up to 2^20) over a batch that spans
+    several chunks of different lengths and ends in a ragged one: equal to
+    the device entry point bit for bit."""
+    n = 65536 + 81920 + 102400 + 128000 + 12345
+    A = inputs.mixed(n, seed=904)[0]
+    At = torch.from_numpy(A)
+    lam_d, U_d = syev3.syev3_batched(At.cuda())
+    torch.cuda.synchronize()
+    Ah = At.pin_memory()
+    lam = torch.empty((n, 3), dtype=At.dtype).pin_memory()
+    U = torch.empty((n, 3, 3), dtype=At.dtype).pin_memory()
+    syev3.syev3_batched_host(Ah, lam, U)
+    assert torch.equal(lam, lam_d.cpu()) and torch.equal(U, U_d.cpu())
+
+
 def test_extreme_magnitudes(syev3):
     """The pre-scale and unscale fallbacks (scalbn): largest entries at or
     above 2^1022, wholly subnormal matrices (outputs subnormal), and single
