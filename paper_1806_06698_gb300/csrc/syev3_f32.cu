@@ -137,23 +137,35 @@ __device__ __forceinline__ Lane32 make_lane32(const float a_in[6]) {
     return L;
   }
   // Sec. 1.1: |abar b1 b2| <= C eps |a1 + a2| h^2.
+  const float h2 = fmaf(b1, b1, b2 * b2);
+  const float lhs = fabsf((L.a1 - L.a2) * b1 * b2);
+  const float rhs = (kCDefl32 * kEps32) * fabsf(L.a1 + L.a2) * h2;
   if (kComp) {
-    // Double-float products: the decision sees the exact sides to ~2^-46.
-    const F2 ab = two_sum(L.a1, -L.a2);
-    const F2 lhs = ff_mul1(ff_mul1(ab, b1), b2);
-    const F2 sum12 = two_sum(L.a1, L.a2);
-    const F2 h2 = ff_add(two_prod(b1, b1), two_prod(b2, b2));
-    F2 rhs = ff_mul(sum12, h2);
-    rhs.h *= kCDefl32 * kEps32;
-    rhs.l *= kCDefl32 * kEps32;
-    const F2 al = {fabsf(lhs.h), lhs.h < 0.f ? -lhs.l : lhs.l};
-    const F2 ar = {fabsf(rhs.h), rhs.h < 0.f ? -rhs.l : rhs.l};
-    L.cls = ff_le(al, ar) ? kDefl : kRed;
-    L.near_defl = (al.h < kNearDefl * ar.h) && (al.h * kNearDefl > ar.h);
+    // The decision of the exact sides (exact arithmetic on the FP32 arrow).
+    // The FP32 sides above carry 3 and 4 roundings, a relative error below
+    // 7 x 2^-24 together, and every intermediate is normal when both sides
+    // are >= 2^-120; sides further apart than a factor 1 + 2^-20 (one more
+    // rounding in forming the bounds) are therefore ordered as the exact
+    // ones.  Closer sides, or sides near underflow, are decided with
+    // double-float products, which carry the exact sides to ~2^-46.
+    const bool clear = lhs >= 0x1p-120f && rhs >= 0x1p-120f &&
+                       (lhs <= rhs * (1.f - 0x1p-20f) || lhs >= rhs * (1.f + 0x1p-20f));
+    if (clear) {
+      L.cls = (lhs <= rhs) ? kDefl : kRed;
+    } else {
+      const F2 ab = two_sum(L.a1, -L.a2);
+      const F2 dl = ff_mul1(ff_mul1(ab, b1), b2);
+      const F2 sum12 = two_sum(L.a1, L.a2);
+      const F2 dh2 = ff_add(two_prod(b1, b1), two_prod(b2, b2));
+      F2 dr = ff_mul(sum12, dh2);
+      dr.h *= kCDefl32 * kEps32;
+      dr.l *= kCDefl32 * kEps32;
+      const F2 al = {fabsf(dl.h), dl.h < 0.f ? -dl.l : dl.l};
+      const F2 ar = {fabsf(dr.h), dr.h < 0.f ? -dr.l : dr.l};
+      L.cls = ff_le(al, ar) ? kDefl : kRed;
+    }
+    L.near_defl = (lhs < kNearDefl * rhs) && (lhs * kNearDefl > rhs);
   } else {
-    const float h2 = fmaf(b1, b1, b2 * b2);
-    const float lhs = fabsf((L.a1 - L.a2) * b1 * b2);
-    const float rhs = (kCDefl32 * kEps32) * fabsf(L.a1 + L.a2) * h2;
     L.cls = (lhs <= rhs) ? kDefl : kRed;
   }
   return L;
@@ -230,22 +242,38 @@ __device__ bool roots32_more(const float ab, const float b1, const float b2, con
 }
 
 // Double-float value of the spectral function at x (FP32 data exact), and
-// one Newton correction x - f/f' with it (Sec. 1.4.2).
+// one Newton correction x - f/f' with it (Sec. 1.4.2).  Each term is formed
+// as an unevaluated pair (head, low part) without renormalisation, and the
+// terms are added by cascaded summation (Ogita, Rump and Oishi 2005,
+// "Sum2"): the heads with TwoSum, every rounding error and low part in one
+// FP32 sum, so f comes out as if summed in twice the working precision and
+// rounded once.  Data pairs (ab, b1, b2, g, c, K) need not be normalised.
 __device__ __forceinline__ float newton_ff(const F2 ab, const F2 b1, const F2 b2, const F2 g, const F2 c, const F2 K,
                                           const float x) {
   const float r1 = rcp32(x);
-  const F2 s = ff_add(two_sum(x, ab.h), {ab.l, 0.f});  // x + ab
-  const float r2 = rcp32(s.h);
-  const F2 xf = {x, 0.f};
-  const F2 t1 = ff_div(b1, xf, r1);
+  const F2 s0 = two_sum(x, ab.h);
+  const float sh = s0.h, sl = s0.l + ab.l;  // x + ab
+  const float r2 = rcp32(sh);
+  // b1 / x: the quotient's head and the remainder over x.
+  const float q1 = b1.h * r1;
+  const float q1l = (fmaf(-q1, x, b1.h) + b1.l) * r1;
+  // Last term: + c x / (x + ab) for x < ab (the cancellation-free form),
+  // - b2 / (x + ab) otherwise; numerator (nh, nl), quotient (q2, q2l).
   const bool small = x < ab.h;
-  F2 acc = ff_add(xf, small ? K : ff_neg(g));
-  acc = ff_add(acc, ff_neg(t1));
-  const F2 last = small ? ff_div(ff_mul1(c, x), s, r2) : ff_neg(ff_div(b2, s, r2));
-  acc = ff_add(acc, last);
-  const float f = acc.h + acc.l;
-  const float t1h = t1.h, t2h = b2.h * r2;
-  const float fp = fmaf(t2h, r2, fmaf(t1h, r1, 1.f));
+  const float cx = c.h * x;
+  const float nh = small ? cx : b2.h;
+  const float nl = small ? fmaf(c.h, x, -cx) + c.l * x : b2.l;
+  const float q2 = nh * r2;
+  const float q2l = ((fmaf(-q2, sh, nh) + nl) - q2 * sl) * r2;
+  const float th = small ? q2 : -q2, tl = small ? q2l : -q2l;
+  // Leading part: K (small) or -g.
+  const float lh = small ? K.h : -g.h, ll = small ? K.l : -g.l;
+  // Sum2 over x + lead - b1/x + last.
+  const F2 u = two_sum(x, lh);
+  const F2 v = two_sum(u.h, -q1);
+  const F2 w = two_sum(v.h, th);
+  const float f = w.h + (((u.l + v.l) + (w.l + ll)) + (tl - q1l));
+  const float fp = fmaf(b2.h * r2, r2, fmaf(q1, r1, 1.f));
   const float xn = x - f * rcp32(fp);
   return (xn > 0.f) ? xn : x;
 }
@@ -436,9 +464,15 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
   __shared__ alignas(16) float s_in[2][kTPB * 6];
   __shared__ alignas(16) float s_lam[kTPB * 3];
   __shared__ alignas(16) float s_U[kTPB * 9];
-  // Compensated form: flagged lanes for the FP64 refinement (arrow, roots, owner).
-  __shared__ float s_fa[kMode == kInline ? 9 * kTPB : 1];
-  __shared__ int s_fi[kMode == kInline ? 2 * kTPB : 1];
+  // Compensated form, refinement in the kernel: the list of flagged lanes,
+  // kFA floats each (arrow, roots, then the input record for the residual
+  // check), their codes and global indices.  Slots [0, nfc) hold the lanes
+  // carried from earlier tiles (fewer than 32), then this tile's.
+  constexpr int kFA = 15, kFW = kTPB + 32;
+  constexpr bool kInl = kMode == kInline;
+  __shared__ float s_fa[kInl ? kFA * kFW : 1];
+  __shared__ int s_fc[kInl ? kFW : 1];
+  __shared__ int64_t s_fg[kInl ? kFW : 1];
   __shared__ int s_nflag;
   // Roots that need more steps than the fixed schedule: (ab, b1, b2, g, x).
   __shared__ float s_more[2 * kTPB * 5];
@@ -476,6 +510,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
   };
 
   uint32_t phases = 0u;
+  int nfc = 0;  // flagged lanes carried into this tile (CTA-uniform)
   int buf = 0;
   int64_t tile = blockIdx.x;
   if (kBulkIn && tid == 0 && tile < n_tiles) issue(tile, 0);
@@ -572,8 +607,17 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
         const float rabh = rcp32(abf.h);
         const F2 fb1 = two_prod(L.b1, L.b1), fb2 = two_prod(L.b2, L.b2);
         const F2 fg0 = two_sum(L.g, -L.a1), fg1 = two_sum(L.a2, -L.g);
-        const F2 fc0 = ff_div(fb2, abf, rabh), fc1 = ff_div(fb1, abf, rabh);
-        const F2 fK0 = ff_neg(ff_add(fg0, fc0)), fK1 = ff_neg(ff_add(fg1, fc1));
+        // c = b2 / abar and K = -(g + c) as unnormalised pairs.
+        auto div_pair = [rabh, abf](const F2 num) {
+          const float q = num.h * rabh;
+          return F2{q, ((fmaf(-q, abf.h, num.h) + num.l) - q * abf.l) * rabh};
+        };
+        auto neg_sum_pair = [](const F2 a, const F2 b) {
+          const F2 t = two_sum(a.h, b.h);
+          return F2{-t.h, -((t.l + a.l) + b.l)};
+        };
+        const F2 fc0 = div_pair(fb2), fc1 = div_pair(fb1);
+        const F2 fK0 = neg_sum_pair(fg0, fc0), fK1 = neg_sum_pair(fg1, fc1);
         root[0] = newton_ff(abf, fb1, fb2, fg0, fc0, fK0, root[0]);
         root[1] = newton_ff(abf, fb2, fb1, fg1, fc1, fK1, root[1]);
       }
@@ -627,34 +671,56 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
         flag_list[wbase + __popc(m & lt_mask)] = r;
       }
     } else if (kComp) {
-      // Compact the flagged lanes and refine them in FP64 with every lane of
-      // the CTA available.
+      // Compact the flagged lanes after the carried ones and refine a whole
+      // number of warps' worth of them in FP64, with every lane of the CTA
+      // available; the rest (fewer than 32) are carried to the next tile, so
+      // no warp runs the FP64 code with idle lanes.  A lane of this tile
+      // gets its refined result in the staging area, a carried one straight
+      // in memory (over the FP32 result written with its own tile).  The
+      // CTA refines its last carried lanes after its final tile.
       const unsigned m = __ballot_sync(0xffffffffu, flagged);
       int wbase = 0;
       if (lane_id == 0 && m) wbase = atomicAdd(&s_nflag, __popc(m));
       wbase = __shfl_sync(0xffffffffu, wbase, 0);
       if (flagged) {
-        const int slot = wbase + __popc(m & lt_mask);
-        float* f = &s_fa[slot * 9];
+        const int slot = nfc + wbase + __popc(m & lt_mask);
+        float* f = &s_fa[slot * kFA];
         f[0] = L.a1; f[1] = L.a2; f[2] = L.b1; f[3] = L.b2; f[4] = L.g; f[5] = L.c; f[6] = L.s;
         f[7] = root[0]; f[8] = root[1];
-        s_fi[slot * 2] = tid;
-        s_fi[slot * 2 + 1] = (L.e << 2) | L.cls;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) f[9 + k] = a_in[k];
+        s_fc[slot] = (L.e << 2) | L.cls;
+        s_fg[slot] = base + tid;
       }
       __syncthreads();
-      const int nf = s_nflag;
-      for (int i = tid; i < nf; i += kTPB) {
-        const int owner = s_fi[i * 2];
+      const int n_avail = nfc + s_nflag;
+      const int P = n_avail & ~31;
+      for (int i = tid; i < P; i += kTPB) {
         double lam[3], U[9];
         // The residual check (counter [3]) only when counters are asked for.
-        const bool bad = refine_one(&s_fa[i * 9], s_fi[i * 2 + 1],
-                                    counters != nullptr ? &s_in[buf][owner * 6] : nullptr, lam, U);
+        const bool bad = refine_one(&s_fa[i * kFA], s_fc[i], counters != nullptr ? &s_fa[i * kFA + 9] : nullptr,
+                                    lam, U);
         if (bad) atomicAdd(&counters[3], 1ull);
+        const int64_t gi = s_fg[i], row = gi - base;
+        const bool here = row >= 0 && row < cnt;
+        float* dl = here ? &s_lam[row * 3] : lam_out + gi * 3;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) s_lam[owner * 3 + k] = (float)lam[k];
+        for (int k = 0; k < 3; ++k) dl[k] = (float)lam[k];
+        if (here || want_U) {
+          float* dU = here ? &s_U[row * 9] : U_out + gi * 9;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) s_U[owner * 9 + k] = (float)U[k];
+          for (int k = 0; k < 9; ++k) dU[k] = (float)U[k];
+        }
       }
+      __syncthreads();
+      const int nc_next = n_avail - P;
+      if (P > 0 && tid < nc_next) {  // [P, n_avail) -> [0, nc_next): no overlap, P >= 32 > nc_next
+#pragma unroll
+        for (int k = 0; k < kFA; ++k) s_fa[tid * kFA + k] = s_fa[(P + tid) * kFA + k];
+        s_fc[tid] = s_fc[P + tid];
+        s_fg[tid] = s_fg[P + tid];
+      }
+      nfc = nc_next;
     }
     if (counters != nullptr) {
       const unsigned cm = __ballot_sync(0xffffffffu, capped);
@@ -697,6 +763,23 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
       }
     }
     __syncthreads();
+  }
+  if (kInl) {
+    // The flagged lanes still carried after the CTA's final tile (nfc is
+    // CTA-uniform; the list was completed before the loop's last barrier).
+    for (int i = tid; i < nfc; i += kTPB) {
+      double lam[3], U[9];
+      const bool bad = refine_one(&s_fa[i * kFA], s_fc[i], counters != nullptr ? &s_fa[i * kFA + 9] : nullptr,
+                                  lam, U);
+      if (bad) atomicAdd(&counters[3], 1ull);
+      const int64_t gi = s_fg[i];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) lam_out[gi * 3 + k] = (float)lam[k];
+      if (want_U) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) U_out[gi * 9 + k] = (float)U[k];
+      }
+    }
   }
 }
 
