@@ -100,8 +100,10 @@ int syev3_batched_ex(const void* A_packed6, int64_t n, void* lambda, void* U, in
  * workspace.  For SYEV3_F32_COMPENSATED the FP64 refinement of flagged lanes
  * (not in the paper: see SYEV3_F32_COMPENSATED) then runs as a second kernel
  * over a list of those lanes kept in the workspace, so the FP32 kernel holds
- * no FP64 code (fewer registers, more resident warps) and the refinement
- * runs in full warps; results equal those of syev3_batched up to rounding.
+ * no FP64 code (fewer registers, more resident warps): the faster path when
+ * few lanes are flagged (syev3_batched refines them in the FP32 kernel, in
+ * whole warps gathered across tiles, and is the faster one when many are).
+ * Results equal those of syev3_batched up to rounding.
  * Other dtypes ignore the workspace (it may be NULL).
  *   d_workspace     : device, at least syev3_workspace_bytes(n, dtype) bytes,
  *                     256-byte aligned, caller-owned; must not overlap the
