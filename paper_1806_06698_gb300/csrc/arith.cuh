@@ -113,8 +113,6 @@ __device__ __forceinline__ F2 ff_add(F2 x, F2 y) {
   return fast_two_sum(s.h, s.l + (x.l + y.l));
 }
 
-__device__ __forceinline__ F2 ff_neg(F2 x) { return {-x.h, -x.l}; }
-
 __device__ __forceinline__ F2 ff_mul(F2 x, F2 y) {
   const F2 p = two_prod(x.h, y.h);
   return fast_two_sum(p.h, fmaf(x.h, y.l, fmaf(x.l, y.h, p.l)));
@@ -123,14 +121,6 @@ __device__ __forceinline__ F2 ff_mul(F2 x, F2 y) {
 __device__ __forceinline__ F2 ff_mul1(F2 x, float y) {
   const F2 p = two_prod(x.h, y);
   return fast_two_sum(p.h, fmaf(x.l, y, p.l));
-}
-
-// x / y with one correction: q = x.h / y.h, remainder x - q y formed exactly
-// to first order, q + remainder / y.
-__device__ __forceinline__ F2 ff_div(F2 x, F2 y, float ry /* ~1/y.h */) {
-  const float q = x.h * ry;
-  const float r = (fmaf(-q, y.h, x.h) + x.l) - q * y.l;
-  return fast_two_sum(q, r * ry);
 }
 
 __device__ __forceinline__ bool ff_le(F2 x, F2 y) { return x.h < y.h || (x.h == y.h && x.l <= y.l); }

@@ -234,6 +234,45 @@ def test_workspace_path_matches_single_kernel(syev3):
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("n", [1, 31, 33, 129, 5_000, 40_001])
+@pytest.mark.parametrize("vectors", [True, False])
+def test_inline_refinement_carry(syev3, n, vectors):
+    """The compensated kernel refines its flagged lanes in whole warps,
+    carrying the rest from tile to tile and refining the last group after
+    the CTA's final tile.  On batches of the clustered subset only (most
+    lanes flagged: carries every tile), at sizes below one warp, across a
+    tile boundary and with ragged ends, and with eigenvalues only (a
+    carried lane then writes no vector): the same counters and results as
+    the workspace path (the refinement as a second kernel), and the FP32
+    bar against the oracle."""
+    A, ids = inputs.mixed_fp32(6 * n + 200, seed=2112)  # 20 % clustered
+    A = np.ascontiguousarray(A[ids == 1][:n])
+    assert A.shape[0] == n
+    At = torch.from_numpy(A).cuda()
+    c1 = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device="cuda")
+    lam1, U1 = syev3.syev3_batched(At, compensated=True, counters=c1, vectors=vectors)
+    nb = syev3.workspace_bytes(n, At.dtype, compensated=True)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    c2 = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device="cuda")
+    lam2, U2 = syev3.syev3_batched(At, compensated=True, counters=c2, workspace=ws, vectors=vectors)
+    torch.cuda.synchronize()
+    assert torch.equal(c1, c2)
+    if n >= 129:
+        assert int(c1[2]) > n // 2  # most lanes refined in FP64
+    scale = float(lam1.abs().max())
+    assert float((lam1 - lam2).abs().max()) <= 4 * parity.EPS32 * scale
+    lam_o, U_o = oracle.syev3(A.astype(np.float64))
+    if vectors:
+        # Vectors of (numerically) repeated eigenvalues are not unique: each
+        # path against the oracle, with the gap filter.
+        vec_gap_filtered_compare(A, lam1.cpu().numpy(), U1.cpu().numpy(), lam_o, U_o)
+        vec_gap_filtered_compare(A, lam2.cpu().numpy(), U2.cpu().numpy(), lam_o, U_o)
+    else:
+        assert U1 is None and U2 is None
+        parity.compare(A.astype(np.float64), lam1.cpu().numpy(), None, lam_o, None, eps=parity.EPS32,
+                       lam_tol=64, res_tol=0, orth_tol=0, vec_tol=0)
+
+
 def test_batch_beyond_32_bit_element_indices(syev3):
     """n = 2^29 FP32 matrices (eigenvector elements up to 4.8e9 > 2^32): the
     kernels' 64-bit index arithmetic.  Inputs are generated on the device;
