@@ -92,18 +92,14 @@ template <bool kComp>
 __device__ __forceinline__ Lane32 make_lane32(const float a_in[6]) {
   Lane32 L;
   L.near_defl = false;
-  int E = 0;
-  bool finite = true;
+  unsigned mag = 0u;  // largest |a_ij| as a bit pattern (orders like |a_ij|)
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    const int ex = (__float_as_int(a_in[i]) >> 23) & 0xff;
-    finite &= (ex != 0xff);
-    E = max(E, ex);
-  }
-  if (!finite) {
+  for (int i = 0; i < 6; ++i) mag = max(mag, __float_as_uint(a_in[i]) & 0x7fffffffu);
+  if (mag >= 0x7f800000u) {  // an infinite or NaN entry
     L.cls = kNonFin;
     return L;
   }
+  const int E = (int)(mag >> 23);
   float a[6];
   if (E >= 1 && E <= 252) {  // exact power-of-two pre-scale: largest entry in [0.5, 1)
     L.e = E - 126;
@@ -388,22 +384,33 @@ __device__ __forceinline__ void finish32(const Lane32& L, float mu, float nu, fl
   cswap(l0, x00, x01, x02, l1, x10, x11, x12);
   const float ls[3] = {l0, l1, l2};
   const float xs[3][3] = {{x00, x01, x02}, {x10, x11, x12}, {x20, x21, x22}};
+  // Sign rule: each column's largest-magnitude component (the first of
+  // equals) made positive, by XOR-ing the column's sign bits with that
+  // component's (never zero: at least 1/sqrt(3) in a unit vector).
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const float y0 = xs[k][0], y1 = xs[k][1], y2 = xs[k][2];
-    float big = y0;
-    if (fabsf(y1) > fabsf(big)) big = y1;
-    if (fabsf(y2) > fabsf(y0) && fabsf(y2) > fabsf(y1)) big = y2;
-    const float sg = (big < 0.f) ? -1.f : 1.f;
+    float big = (fabsf(y1) > fabsf(y0)) ? y1 : y0;
+    big = (fabsf(y2) > fabsf(big)) ? y2 : big;
+    const unsigned sb = __float_as_uint(big) & 0x80000000u;
     l_out[k] = ls[k];
-    U[0 * 3 + k] = sg * y0;
-    U[1 * 3 + k] = sg * y1;
-    U[2 * 3 + k] = sg * y2;
+    U[0 * 3 + k] = __uint_as_float(__float_as_uint(y0) ^ sb);
+    U[1 * 3 + k] = __uint_as_float(__float_as_uint(y1) ^ sb);
+    U[2 * 3 + k] = __uint_as_float(__float_as_uint(y2) ^ sb);
   }
 }
 
-__device__ __forceinline__ float unscale32(float v, int e) {
-  return (e >= -126 && e <= 127) ? v * pow2f(e) : scalbnf(v, e);
+// Eigenvalues back to the input's scale, l * 2^e: one exact multiply when
+// 2^e is a normal float, scalbnf otherwise (the range check once per lane).
+__device__ __forceinline__ void unscale3(float l[3], int e) {
+  if (e >= -126 && e <= 127) {
+    const float sc = pow2f(e);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) l[k] *= sc;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) l[k] = scalbnf(l[k], e);
+  }
 }
 
 // FP64 refinement of one flagged lane (compensated form): the arrow and the
@@ -635,8 +642,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
         for (int k = 0; k < 9; ++k) U[k] = qnan;
       } else if (!kVectors) {
         finish32_values(L, root[0], root[1], l);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) l[k] = unscale32(l[k], L.e);
+        unscale3(l, L.e);
       } else {
         finish32(L, root[0], root[1], l, U);
         if (kComp && L.cls != kDiag) {
@@ -644,8 +650,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
           const float gap = fminf(l[1] - l[0], l[2] - l[1]);
           flagged = capped || L.near_defl || (gap * gap < (kClusterTau * kClusterTau) * nrm2);
         }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) l[k] = unscale32(l[k], L.e);
+        unscale3(l, L.e);
       }
 #pragma unroll
       for (int k = 0; k < 3; ++k) s_lam[tid * 3 + k] = l[k];
