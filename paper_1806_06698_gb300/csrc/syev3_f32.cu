@@ -9,8 +9,10 @@
 // (see solve_f64.cuh).
 //
 // The compensated form (SYEV3_F32_COMPENSATED) adds, in FP32:
-//  * double-float (error-free transformation) products in the deflation
-//    test of Sec. 1.1, so the decision is not blurred by FP32 rounding;
+//  * the deflation test of Sec. 1.1 decided as on exact products, so the
+//    decision is not blurred by FP32 rounding: on the FP32 sides where they
+//    are clearly apart, with double-float (error-free transformation)
+//    products where they are close;
 //  * a double-float evaluation of the spectral function at the FP32 root
 //    and one Newton correction (Sec. 1.4.2) with it;
 // and uses FP64 only on the lanes it flags -- near-deflated (the test's two
@@ -18,13 +20,15 @@
 // below kClusterTau) or capped -- for a final FP64 Newton step on mu and nu,
 // eigenvectors re-formed (and so re-orthogonalised) in FP64 and an FP64
 // residual check against the input.  Flagged lanes are compacted with warp
-// ballots into a shared-memory list so the FP64 work runs on as few warps as
-// possible; no global scratch memory is used.
+// ballots into a shared-memory list and refined in whole warps, the rest
+// carried from tile to tile, so the FP64 work runs on as few warps as
+// possible; no global scratch memory is used (syev3_batched_ws instead
+// appends them to a list in a workspace for k_refine_f32).
 //
 // Memory path as in the FP64 kernel: tiles of kTPB records (24 B each) by
 // 1-D bulk copy into shared memory, double-buffered on mbarriers; results
 // staged in shared memory and written with 16-byte stores.  The plain form
-// moves 72 B per matrix and is bound by HBM bandwidth.
+// moves 72 B per matrix; it is bound by instruction issue, not by HBM.
 
 #include <cmath>
 #include <cstdint>
