@@ -652,9 +652,13 @@ def run_native(args):
     def e2e_step():
         syev3.syev3_batched_host(A_host, lam_host, U_host, stream=stream)
 
-    e2e_ms, _ = _timed(e2e_step, e2e_steps, 1, stream, barrier)
+    e2e_ms, e2e_each = _timed(e2e_step, e2e_steps, 1, stream, barrier)
     e2e_ms = max_over_ranks(e2e_ms, dev)
     e2e_value = whole_job_rate(n, ws, e2e_steps, e2e_ms)
+    # The host link is shared with other jobs on the machine: the spread of
+    # the steps shows whether a slow run was contention (a few slow steps)
+    # or the pipeline (all steps alike).  The value stays the whole run.
+    e2e_each = sorted(e2e_each)
 
     # Eigenvalues only (U = NULL): the same batch, no eigenvectors formed or
     # written (24 B out per matrix).
@@ -699,7 +703,9 @@ def run_native(args):
             "gpu_launches": args.steps,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 48,
                     "d2h_bytes_per_step": n * 96, "api": "syev3_batched_host (pinned host buffers, "
-                    "3-stream copy/solve pipeline, chunks of 2^16 growing by a quarter to 2^20)"},
+                    "3-stream copy/solve pipeline, chunks of 2^16 growing by a quarter to 2^20)",
+                    "steps": e2e_steps, "ms_per_step": e2e_ms / e2e_steps,
+                    "ms_per_step_min": e2e_each[0], "ms_per_step_median": e2e_each[len(e2e_each) // 2]},
             "clocks": clocks,
         }
         line["eigenvalues_only"] = values_only

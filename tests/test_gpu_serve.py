@@ -84,11 +84,15 @@ def test_small_requests_overtake_a_large_one(syev3, pools):
     """Continuous batching: requests that arrive while a large request is on
     the device are admitted and finish before it does."""
     A64, _ = pools
-    srv = syev3.Server(memory_budget_bytes=1 << 30, num_streams=4, chunk=1 << 14, max_inflight=1)
-    big = srv.submit(A64)  # 2^20 matrices, 64 chunks
+    # 2^23 matrices in 512 chunks: about 3.4 ms of solving, long against the
+    # time the host takes to submit the small requests below.
+    A_big = A64.repeat(8, 1)
+    srv = syev3.Server(memory_budget_bytes=2 << 30, num_streams=4, chunk=1 << 14, max_inflight=1)
+    big = srv.submit(A_big)
     while srv.query(big).state == 0:
         time.sleep(0.0001)
     small = [srv.submit(A64[i * 97:(i * 97) + 64]) for i in range(16)]
+    assert srv.query(big).state == 1  # the small requests arrived while it ran
     done_small = [srv.wait(t, 60.0).t_done_ns for t in small]
     done_big = srv.wait(big, 60.0).t_done_ns
     assert max(done_small) < done_big
