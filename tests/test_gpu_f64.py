@@ -257,6 +257,23 @@ def test_host_entry_point_default_schedule(syev3):
     assert torch.equal(lam, lam_d.cpu()) and torch.equal(U, U_d.cpu())
 
 
+def test_host_entry_point_full_size(syev3):
+    """The end-to-end path at the benchmark's size: 2^24 mixed FP64 matrices
+    from pinned host buffers through the default chunk schedule (25 chunks),
+    equal bit for bit to the device entry point on the same matrices."""
+    n = 1 << 24
+    A = inputs.mixed(n)[0]
+    Ah = torch.from_numpy(A).pin_memory()
+    lam = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    U = torch.empty((n, 3, 3), dtype=torch.float64).pin_memory()
+    syev3.syev3_batched_host(Ah, lam, U)
+    Ad = Ah.cuda()
+    lam_d, U_d = syev3.syev3_batched(Ad)
+    torch.cuda.synchronize()
+    assert torch.equal(lam, lam_d.cpu())
+    assert torch.equal(U, U_d.cpu())
+
+
 def test_extreme_magnitudes(syev3):
     """The pre-scale and unscale fallbacks (scalbn): largest entries at or
     above 2^1022, wholly subnormal matrices (outputs subnormal), and single
