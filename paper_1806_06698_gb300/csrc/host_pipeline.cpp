@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/syev3.h"
+#include "internal.h"
 
 namespace {
 
@@ -47,11 +48,8 @@ struct Staging {
 
 Staging g_staging[kMaxDevices];
 
-int host_fail(cudaError_t e) {
-  (void)e;
-  cudaGetLastError();
-  return SYEV3_ECUDA;
-}
+// Records the CUDA error for syev3_last_cuda_error and returns SYEV3_ECUDA.
+int host_fail(cudaError_t e) { return syev3::record_cuda_error(e); }
 
 }  // namespace
 
@@ -69,7 +67,8 @@ int syev3_batched_host(const void* A_host, int64_t n, void* lambda_host, void* U
   const size_t lam_off = (size_t)chunk * in_b, U_off = lam_off + ((size_t)chunk * lam_b + 255) / 256 * 256;
   const size_t need = U_off + (U_host ? (size_t)chunk * U_b : 0);
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return host_fail(cudaErrorInvalidDevice);
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return host_fail(e);
   if (dev < 0 || dev >= kMaxDevices) return SYEV3_EINVAL;
   Staging* S = &g_staging[dev];
   // Calls for the same device from several host threads run one after another.
@@ -79,24 +78,48 @@ int syev3_batched_host(const void* A_host, int64_t n, void* lambda_host, void* U
       for (int k = 0; k < kStreams; ++k) {
         if (S->buf[k]) cudaFree(S->buf[k]);
         S->buf[k] = nullptr;
-        if (cudaMalloc(&S->buf[k], need) != cudaSuccess) {
+        e = cudaMalloc(&S->buf[k], need);
+        if (e != cudaSuccess) {
+          S->buf[k] = nullptr;
           S->bytes = 0;
-          return host_fail(cudaErrorMemoryAllocation);
+          return host_fail(e);
         }
       }
       S->bytes = need;
     }
-    for (int k = 0; k < kStreams; ++k)
-      if (!S->st[k] && cudaStreamCreateWithFlags(&S->st[k], cudaStreamNonBlocking) != cudaSuccess)
-        return host_fail(cudaErrorUnknown);
-    if (!S->start && cudaEventCreateWithFlags(&S->start, cudaEventDisableTiming) != cudaSuccess)
-      return host_fail(cudaErrorUnknown);
+    for (int k = 0; k < kStreams; ++k) {
+      if (S->st[k]) continue;
+      e = cudaStreamCreateWithFlags(&S->st[k], cudaStreamNonBlocking);
+      if (e != cudaSuccess) {
+        S->st[k] = nullptr;
+        return host_fail(e);
+      }
+    }
+    if (!S->start) {
+      e = cudaEventCreateWithFlags(&S->start, cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        S->start = nullptr;
+        return host_fail(e);
+      }
+    }
   }
+  // A failure once work is queued first waits for the library's streams:
+  // copies already in flight read and write the caller's host buffers,
+  // which the caller may free or reuse as soon as this returns.
+  auto drain = [&]() {
+    for (int k = 0; k < kStreams; ++k) cudaStreamSynchronize(S->st[k]);
+  };
   // Order after the caller's stream, then run the pipeline.
   cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaEventRecord(S->start, user) != cudaSuccess) return host_fail(cudaErrorUnknown);
-  for (int k = 0; k < kStreams; ++k)
-    if (cudaStreamWaitEvent(S->st[k], S->start, 0) != cudaSuccess) return host_fail(cudaErrorUnknown);
+  e = cudaEventRecord(S->start, user);
+  if (e != cudaSuccess) return host_fail(e);
+  for (int k = 0; k < kStreams; ++k) {
+    e = cudaStreamWaitEvent(S->st[k], S->start, 0);
+    if (e != cudaSuccess) {
+      drain();
+      return host_fail(e);
+    }
+  }
   const char* A = static_cast<const char*>(A_host);
   char* L = static_cast<char*>(lambda_host);
   char* V = static_cast<char*>(U_host);
@@ -107,18 +130,28 @@ int syev3_batched_host(const void* A_host, int64_t n, void* lambda_host, void* U
     if (ramp) c = next_chunk(c);
     char* d = S->buf[k];
     cudaStream_t s = S->st[k];
-    if (cudaMemcpyAsync(d, A + b * in_b, cnt * in_b, cudaMemcpyHostToDevice, s) != cudaSuccess)
-      return host_fail(cudaErrorUnknown);
-    const int st = syev3_batched(d, cnt, d + lam_off, V ? d + U_off : nullptr, dtype,
-                                 reinterpret_cast<syev3_stream_t>(s));
-    if (st != SYEV3_OK) return st;
-    if (cudaMemcpyAsync(L + b * lam_b, d + lam_off, cnt * lam_b, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-      return host_fail(cudaErrorUnknown);
-    if (V && cudaMemcpyAsync(V + b * U_b, d + U_off, cnt * U_b, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-      return host_fail(cudaErrorUnknown);
+    e = cudaMemcpyAsync(d, A + b * in_b, cnt * in_b, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+      const int st = syev3_batched(d, cnt, d + lam_off, V ? d + U_off : nullptr, dtype,
+                                   reinterpret_cast<syev3_stream_t>(s));
+      if (st != SYEV3_OK) {  // the launch's error is recorded already
+        drain();
+        return st;
+      }
+      e = cudaMemcpyAsync(L + b * lam_b, d + lam_off, cnt * lam_b, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess && V) e = cudaMemcpyAsync(V + b * U_b, d + U_off, cnt * U_b, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) {
+      drain();
+      return host_fail(e);
+    }
   }
-  for (int k = 0; k < kStreams; ++k)
-    if (cudaStreamSynchronize(S->st[k]) != cudaSuccess) return host_fail(cudaErrorUnknown);
+  cudaError_t first = cudaSuccess;
+  for (int k = 0; k < kStreams; ++k) {
+    e = cudaStreamSynchronize(S->st[k]);
+    if (e != cudaSuccess && first == cudaSuccess) first = e;
+  }
+  if (first != cudaSuccess) return host_fail(first);
   return SYEV3_OK;
 }
 
