@@ -240,6 +240,42 @@ int syev3_device_flags(uint32_t* flags);
  * failure handling; not in the paper.  Asynchronous on `stream`. */
 int syev3_selftest_wait_limit(syev3_stream_t stream);
 
+/* syev3_selftest_arith -- the kernels' own approximate arithmetic, applied
+ * elementwise, so tests can hold it to the error bounds the solver relies
+ * on.  Not in the paper.
+ *   op : SYEV3_ARITH_RCP64  -- 1/x in FP64: the hardware's reciprocal
+ *                              estimate refined by one third-order
+ *                              Newton-Raphson step (within 1 ulp of 1/x for
+ *                              2^-1000 < |x| < 2^1000);
+ *        SYEV3_ARITH_RCP32, SYEV3_ARITH_SQRT32, SYEV3_ARITH_RSQRT32 -- the
+ *                              FP32 hardware approximations 1/x, sqrt(x),
+ *                              1/sqrt(x) (flush-to-zero) used by the FP32
+ *                              zero finder.
+ *   x  : device, n elements (double for RCP64, float otherwise), read.
+ *   y  : device, n elements of the same type, written; may not overlap x.
+ *   n  : >= 0.
+ * Returns SYEV3_EINVAL (bad op, n < 0, NULL or misaligned buffers) or
+ * SYEV3_ECUDA; asynchronous on `stream`. */
+#define SYEV3_ARITH_RCP64 0
+#define SYEV3_ARITH_RCP32 1
+#define SYEV3_ARITH_SQRT32 2
+#define SYEV3_ARITH_RSQRT32 3
+
+int syev3_selftest_arith(int op, const void* x, void* y, int64_t n, syev3_stream_t stream);
+
+/* syev3_probe_dfma -- launches one kernel that issues only FP64 fused
+ * multiply-adds (independent chains on every resident thread of every SM)
+ * and stores in *dfma_count the number it executes, so that the caller,
+ * timing the launch on `stream`, obtains the device's FP64 operation rate:
+ * the peak against which the FP64 solver's roofline is reported.  Not in
+ * the paper.
+ *   iters      : iterations per chain, >= 1 (10^5 takes about 10 ms).
+ *   d_sink     : device, 1 double (never written in practice; keeps the
+ *                chains from being optimised away).
+ *   dfma_count : host, written before the launch.
+ * Returns SYEV3_EINVAL or SYEV3_ECUDA on failure. */
+int syev3_probe_dfma(int64_t iters, double* d_sink, int64_t* dfma_count, syev3_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Serving: a continuous-batching request server (not in the paper).
  *

@@ -7,9 +7,16 @@
 namespace syev3 {
 namespace {  // internal linkage: every translation unit gets its own copy
 
-// 1/x: hardware estimate (relative error 2^-20) refined by one cubic
-// Newton-Raphson step, e = 1 - x y, y <- y (1 + e + e^2) (error e^3 ~ 2^-60);
-// within 1 ulp for 2^-1000 < |x| < 2^1000.
+// 1/x: the hardware's reciprocal estimate y (relative error below 2^-20,
+// subnormal results flushed) refined by one step of the third-order
+// Newton-Raphson iteration for the reciprocal: with e = 1 - x y (one FMA,
+// exact to rounding), 1/x = y / (1 - e) = y (1 + e + e^2 + e^3 + ...), and
+// truncating after e^2 leaves a relative error of order e^3 ~ 2^-60 (the
+// classical iteration for division, e.g. Muller et al., Handbook of
+// Floating-Point Arithmetic, 2nd ed. 2018, on Newton-Raphson-based division).
+// The final FMA rounds once, so the result is within 1 ulp of 1/x for
+// 2^-1000 < |x| < 2^1000; syev3_selftest_arith exposes it to the tests that
+// check this against IEEE division.
 __device__ __forceinline__ double rcp64(double x) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
@@ -17,6 +24,9 @@ __device__ __forceinline__ double rcp64(double x) {
   return fma(y, fma(e, e, e), y);
 }
 
+// FP32 hardware approximations (flush-to-zero): 1/x, sqrt(x) and 1/sqrt(x).
+// The FP32 zero finder's error allowances assume each within a few units of
+// 2^-23 relative; syev3_selftest_arith exposes them to the tests of that.
 __device__ __forceinline__ float rcp32(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

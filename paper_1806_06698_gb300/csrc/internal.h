@@ -52,6 +52,11 @@ cudaError_t launch_bwd(const T* lam, const T* U, const T* gl, const T* gU, int64
 // One CTA whose bounded wait runs out (syev3_selftest_wait_limit).
 cudaError_t launch_wait_selftest(cudaStream_t stream);
 
+// The arithmetic helpers of arith.cuh elementwise (syev3_selftest_arith) and
+// the FP64 fused multiply-add rate probe (syev3_probe_dfma); selftest.cu.
+cudaError_t launch_arith_probe(int op, const void* x, void* y, int64_t n, cudaStream_t stream);
+cudaError_t launch_dfma_probe(int64_t iters, double* sink, int64_t* dfma_count, cudaStream_t stream);
+
 // Record e as this host thread's last CUDA error (syev3_last_cuda_error),
 // clear the runtime's last-error state, and return SYEV3_ECUDA.
 int record_cuda_error(cudaError_t e);

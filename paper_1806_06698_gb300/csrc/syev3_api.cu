@@ -186,6 +186,24 @@ int syev3_selftest_wait_limit(syev3_stream_t stream) {
   return e == cudaSuccess ? SYEV3_OK : cuda_fail(e);
 }
 
+int syev3_selftest_arith(int op, const void* x, void* y, int64_t n, syev3_stream_t stream) {
+  if (op < SYEV3_ARITH_RCP64 || op > SYEV3_ARITH_RSQRT32 || n < 0) return SYEV3_EINVAL;
+  if (n == 0) return SYEV3_OK;
+  const size_t es = op == SYEV3_ARITH_RCP64 ? 8 : 4;
+  if (x == nullptr || y == nullptr || !aligned(x, es) || !aligned(y, es) || overlap(x, n * es, y, n * es) ||
+      !device_accessible(x) || !device_accessible(y))
+    return SYEV3_EINVAL;
+  const cudaError_t e = syev3::launch_arith_probe(op, x, y, n, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SYEV3_OK : cuda_fail(e);
+}
+
+int syev3_probe_dfma(int64_t iters, double* d_sink, int64_t* dfma_count, syev3_stream_t stream) {
+  if (iters < 1 || d_sink == nullptr || dfma_count == nullptr || !aligned(d_sink, 8) || !device_accessible(d_sink))
+    return SYEV3_EINVAL;
+  const cudaError_t e = syev3::launch_dfma_probe(iters, d_sink, dfma_count, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SYEV3_OK : cuda_fail(e);
+}
+
 int syev3_device_flags(uint32_t* flags) {
   if (flags == nullptr) return SYEV3_EINVAL;
   cudaError_t e = cudaDeviceSynchronize();

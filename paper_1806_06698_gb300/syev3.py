@@ -73,6 +73,10 @@ def _load():
             lib.syev3_selftest_wait_limit.restype = i32
             lib.syev3_device_flags.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
             lib.syev3_device_flags.restype = i32
+            lib.syev3_selftest_arith.argtypes = [i32, vp, vp, i64, vp]
+            lib.syev3_selftest_arith.restype = i32
+            lib.syev3_probe_dfma.argtypes = [i64, vp, ctypes.POINTER(ctypes.c_int64), vp]
+            lib.syev3_probe_dfma.restype = i32
             _lib = lib
     return _lib
 
@@ -218,6 +222,32 @@ def device_flags() -> int:
     v = ctypes.c_uint32(0)
     _check(lib.syev3_device_flags(ctypes.byref(v)), "syev3_device_flags")
     return int(v.value)
+
+
+# Operations of syev3_selftest_arith (include/syev3.h).
+ARITH_RCP64, ARITH_RCP32, ARITH_SQRT32, ARITH_RSQRT32 = 0, 1, 2, 3
+
+
+def selftest_arith(op: int, x: torch.Tensor, stream=None) -> torch.Tensor:
+    """The kernels' approximate reciprocal / square root helpers applied to
+    the device tensor x (float64 for ARITH_RCP64, float32 otherwise)."""
+    want = torch.float64 if op == ARITH_RCP64 else torch.float32
+    if not x.is_cuda or x.dtype != want or not x.is_contiguous():
+        raise ValueError(f"x must be a contiguous {want} CUDA tensor")
+    y = torch.empty_like(x)
+    _check(_load().syev3_selftest_arith(int(op), _ptr(x), _ptr(y), x.numel(), _stream(stream)),
+           "syev3_selftest_arith")
+    return y
+
+
+def probe_dfma(iters: int, sink: torch.Tensor, stream=None) -> int:
+    """Launch the FP64 fused multiply-add rate probe on ``stream`` (sink: a
+    float64 device tensor of >= 1 element); returns the number of FP64 FMAs
+    the launch executes (time it with events on the same stream)."""
+    cnt = ctypes.c_int64(0)
+    _check(_load().syev3_probe_dfma(int(iters), _ptr(sink), ctypes.byref(cnt), _stream(stream)),
+           "syev3_probe_dfma")
+    return int(cnt.value)
 
 
 def syev3_batched_bwd(lam: torch.Tensor, U: torch.Tensor, g_lam: torch.Tensor, g_U: torch.Tensor | None,

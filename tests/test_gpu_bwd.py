@@ -152,22 +152,52 @@ def test_bwd_rejects_bad_args(syev3):
     assert lib.syev3_batched_bwd(None, 0, None, None, 0, None, 0.0, 0, None) == syev3.SYEV3_OK
 
 
-def test_bwd_full_size_sampled(syev3):
+def fp32_bwd_error(g, ref, lam, gl, gU, tau):
+    """Per matrix, |g - ref| in units of eps32 times the scale the FP32
+    arithmetic of the backward kernel works at: S = max|gl| + max|gU| /
+    (smallest unmasked gap).  The kernel forms M_ij - M_ji with 6 FMAs, the
+    coupling (M_ij - M_ji) / (2 gap) with one rounded difference and one
+    IEEE division, then two 3-term products with U (|U_ij| <= 1); adding up
+    these roundings bounds the error by about 200 eps32 S.  Pairs whose gap
+    lies within a factor 2 of the mask threshold tau ||lambda|| are
+    ambiguous (FP32 and FP64 may decide the mask differently) and returned
+    separately."""
+    lam = lam.astype(np.float64)
+    nl = np.linalg.norm(lam, axis=1)
+    gaps = np.stack([lam[:, 1] - lam[:, 0], lam[:, 2] - lam[:, 0], lam[:, 2] - lam[:, 1]], axis=1)
+    thr = tau * nl[:, None]
+    masked = gaps < thr
+    ambiguous = np.any((gaps > 0.5 * thr) & (gaps < 2.0 * thr), axis=1)
+    gmin = np.min(np.where(masked, np.inf, gaps), axis=1)
+    scale = np.abs(gl).max(axis=1) + np.abs(gU).reshape(len(gU), -1).max(axis=1) / gmin
+    err = np.abs(g - ref).max(axis=1) / scale / parity.EPS32
+    return err, ambiguous
+
+
+def test_bwd_full_size(syev3):
     """2^20 matrices (95 % gaps >= 1e-3, 5 % near-degenerate, masked) in
-    FP64 and FP32, in the benchmark's launch: sampled against the oracle."""
+    FP64 and FP32, in the benchmark's launch, every gradient against the
+    oracle's analytic gradient on the same (lambda, U, g_lambda, g_U):
+    FP64 to 1e-11 relative, FP32 within 256 eps32 of the scale its
+    arithmetic works at (fp32_bwd_error)."""
     A, d, deg = inputs.spectral(1 << 20, seed=3008)
+    n = A.shape[0]
     rng = np.random.default_rng(3009)
-    wn = rng.standard_normal((A.shape[0], 3))
-    Vn = rng.standard_normal((A.shape[0], 3, 3))
-    idx = np.sort(rng.choice(A.shape[0], 1 << 14, replace=False))
-    for dt, tol in ((torch.float64, 1e-11), (torch.float32, None)):
+    wn = rng.standard_normal((n, 3))
+    Vn = rng.standard_normal((n, 3, 3))
+    for dt in (torch.float64, torch.float32):
         _, lam, U = forward(syev3, A.astype(np.float64 if dt == torch.float64 else np.float32), dt)
         w = torch.from_numpy(wn).to("cuda", dt)
         V = torch.from_numpy(Vn).to("cuda", dt)
         g = syev3.syev3_batched_bwd(lam, U, w, V, 1e-6)
         torch.cuda.synchronize()
-        assert bool(torch.isfinite(g).all())
-        if tol is None:
-            continue
-        ref = oracle.syev3_bwd(lam.cpu().numpy()[idx], U.cpu().numpy()[idx], wn[idx], Vn[idx], 1e-6)
-        assert rel_err(g.cpu().numpy()[idx], ref).max() <= tol
+        lam_c, U_c, w_c, V_c = (t.cpu().numpy() for t in (lam, U, w, V))
+        g_c = g.cpu().numpy().astype(np.float64)
+        ref = oracle.syev3_bwd(lam_c.astype(np.float64), U_c.astype(np.float64), w_c.astype(np.float64),
+                               V_c.astype(np.float64), 1e-6)
+        if dt == torch.float64:
+            assert rel_err(g_c, ref).max() <= 1e-11
+        else:
+            err, amb = fp32_bwd_error(g_c, ref, lam_c, w_c.astype(np.float64), V_c.astype(np.float64), 1e-6)
+            assert amb.mean() < 1e-3, amb.sum()
+            assert err[~amb].max() <= 256, float(err[~amb].max())

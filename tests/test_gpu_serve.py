@@ -9,6 +9,8 @@ import time
 import numpy as np
 import pytest
 
+import parity
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -32,16 +34,37 @@ def pools():
     return A64, A32
 
 
+@pytest.fixture(scope="module")
+def pool_oracle(pools):
+    """The oracle's (lambda, U) of every matrix of both pools (the FP32 pool
+    upcast exactly to FP64)."""
+    A64, A32 = pools
+    return (parity.oracle_all_cores(A64.cpu().numpy()),
+            parity.oracle_all_cores(A32.cpu().numpy().astype(np.float64)))
+
+
+def check_against_oracle(A, lam, U, ref):
+    """A served result against the oracle: the FP64 bar for FP64 requests,
+    the FP32 bar (64 eps32) for FP32 ones."""
+    A_np = A.cpu().numpy()
+    lam_o, U_o = ref
+    if A.dtype == torch.float64:
+        parity.compare_f64(A_np, lam.cpu().numpy(), U.cpu().numpy(), lam_o, U_o)
+    else:
+        parity.compare_f32(A_np, lam.cpu().numpy(), U.cpu().numpy(), lam_o, U_o)
+
+
 def standalone(syev3, A, comp):
     lam, U = syev3.syev3_batched(A, compensated=comp)
     torch.cuda.synchronize()
     return lam, U
 
 
-def test_same_alone_and_in_the_mix(syev3, pools):
+def test_same_alone_and_in_the_mix(syev3, pools, pool_oracle):
     """Requests of uneven sizes and mixed dtypes, submitted from a client
     thread while earlier ones run, through a small budget that makes some
-    wait for memory and small chunks that interleave them."""
+    wait for memory and small chunks that interleave them: every result
+    equals a standalone call bit for bit and matches the oracle."""
     A64, A32 = pools
     rng = np.random.default_rng(4002)
     budget = 48 << 20
@@ -52,11 +75,11 @@ def test_same_alone_and_in_the_mix(syev3, pools):
         kind = rng.choice(["f64", "f32", "f32c"], p=[0.6, 0.2, 0.2])
         pool = A64 if kind == "f64" else A32
         off = int(rng.integers(0, pool.shape[0] - n))
-        reqs.append((pool[off:off + n], kind == "f32c"))
+        reqs.append((pool[off:off + n], kind == "f32c", kind == "f64", off))
     tickets = [None] * len(reqs)
 
     def client():
-        for i, (A, comp) in enumerate(reqs):
+        for i, (A, comp, _, _) in enumerate(reqs):
             tickets[i] = srv.submit(A, compensated=comp)
             if i % 7 == 0:
                 time.sleep(0.0005)
@@ -65,13 +88,16 @@ def test_same_alone_and_in_the_mix(syev3, pools):
     th.start()
     th.join()
     waited = 0
-    for i, (A, comp) in enumerate(reqs):
+    for i, (A, comp, is64, off) in enumerate(reqs):
         info = srv.wait(tickets[i], 60.0)
         assert info.state == 2 and info.n == A.shape[0]
         waited += info.t_admit_ns > info.t_submit_ns + 200_000
         lam, U = srv.results(tickets[i])
         lam_s, U_s = standalone(syev3, A, comp)
         assert torch.equal(lam, lam_s) and torch.equal(U, U_s), i
+        lam_o, U_o = pool_oracle[0 if is64 else 1]
+        sl = slice(off, off + A.shape[0])
+        check_against_oracle(A, lam, U, (lam_o[sl], U_o[sl]))
         srv.release(tickets[i])
     st = srv.stats()
     assert st.completed == len(reqs) and st.waiting == 0 and st.error == 0

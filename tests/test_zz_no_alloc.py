@@ -3,7 +3,7 @@ list lives in the library's static device memory, so the call allocates
 nothing.  Collected last (file name), it must also pass alone: nothing here
 depends on what earlier tests did.  Compared with the existing entry point
 syev3_batched (compensated) within the FP32 test tolerance, on two calls in a
-row."""
+row, and with the CPU oracle (the FP32 bar)."""
 
 import ctypes
 
@@ -55,6 +55,7 @@ def test_matches_existing_entry_point_twice(n):
     c_ref = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device="cuda")
     lam_ref, U_ref = syev3.syev3_batched(At, compensated=True, counters=c_ref)
     nrm = torch.from_numpy(parity.fro(A.astype(np.float64))).cuda()
+    lam_o, U_o = parity.oracle_all_cores(A.astype(np.float64))
     for _ in range(2):  # the list's counter is cleared by each call
         c = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device="cuda")
         lam, U = syev3.syev3_batched_static_ws(At, counters=c)
@@ -71,3 +72,4 @@ def test_matches_existing_entry_point_twice(n):
         sel = gap >= 1e-2
         d = torch.minimum((U - U_ref).abs().amax(dim=1), (U + U_ref).abs().amax(dim=1)).amax(dim=1)
         assert float((d[sel].double() * gap[sel]).max()) <= 64 * parity.EPS32
+        parity.compare_f32(A, lam.cpu().numpy(), U.cpu().numpy(), lam_o, U_o)
