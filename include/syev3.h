@@ -54,9 +54,9 @@ typedef enum {
   SYEV3_ECUDA = 2,   /* a CUDA call failed (syev3_last_cuda_error() has the code) */
   SYEV3_ENOCONV = 3, /* reserved: reported through counters, never returned by a launch */
   SYEV3_ETIMEOUT = 4 /* a device-side wait ran out (see syev3_device_flags) */
-} syev3_status;
+} syev3_status;    /* (and SYEV3_EAGAIN, below with the server) */
 
-/* Library ABI version (this header: 1). */
+/* Library ABI version (this header: 2). */
 int syev3_abi_version(void);
 
 /* Human-readable name of a status code (static string). */
@@ -135,7 +135,10 @@ int syev3_batched_ws(const void* A_packed6, int64_t n, void* lambda, void* U, in
  * (other streams or host threads) race on it and must be ordered by the
  * caller.  The first call on a device resolves the array's address
  * (cudaGetSymbolAddress, with that device current); it must come before any
- * stream capture begins on that device.  Errors as syev3_batched_ws. */
+ * stream capture begins on that device.  The address is kept for the life
+ * of the process: do not use this entry point on a device after
+ * cudaDeviceReset (the new context may place the array elsewhere).  Errors
+ * as syev3_batched_ws. */
 #define SYEV3_STATIC_MAX_N 262144
 
 int syev3_batched_static_ws(const void* A_packed6, int64_t n, void* lambda, void* U, uint64_t* d_counters,
@@ -277,24 +280,40 @@ int syev3_selftest_arith(int op, const void* x, void* y, int64_t n, syev3_stream
 int syev3_probe_dfma(int64_t iters, double* d_sink, int64_t* dfma_count, syev3_stream_t stream);
 
 /* ------------------------------------------------------------------------
- * Serving: a continuous-batching request server (not in the paper).
+ * Serving: a continuous-batching request server (not in the paper; each
+ * request's matrices go through the method of Secs. 1-1.4.1).
  *
- * Requests reference packed matrices already in device memory and receive
- * their eigenvalues (and eigenvectors) in a device arena of fixed size -- the
- * memory budget -- allocated once by syev3_server_create.  A dispatcher
- * thread admits waiting requests in arrival order as the arena frees up,
- * cuts them into chunks and issues the chunks round-robin across all
- * admitted requests onto `num_streams` CUDA streams (at most `max_inflight`
- * per stream), so requests arriving while others run share the device.
+ * Requests reference packed matrices already in device memory.  The queues,
+ * the admission state and the results live on the device: a ring of
+ * SYEV3_SERVER_SLOTS request slots, a FIFO admission over them against an
+ * arena of fixed size (the memory budget, allocated once by
+ * syev3_server_create) that receives every request's eigenvalues and
+ * eigenvectors, and per round the list of work the device chose.  The
+ * library's host thread passes new requests and releases to the device and
+ * launches rounds while there is work; in each round the device
+ *  - frees released requests and admits waiting ones in arrival order as far
+ *    as the arena has room,
+ *  - gives every admitted request with work left up to `chunk` matrices
+ *    (round-robin, `round_matrices` in all), and solves them as one ragged
+ *    batch per element type, so requests that arrive while others run share
+ *    the device from their first round on,
+ *  - marks finished requests done, with a device timestamp.
  * Results stay in the arena until syev3_server_release.
  * ------------------------------------------------------------------------ */
 typedef struct syev3_server_s syev3_server;
 
+/* Requests submitted and not yet released, at most. */
+#define SYEV3_SERVER_SLOTS 4096
+
+/* Returned by syev3_server_submit when SYEV3_SERVER_SLOTS requests are
+ * outstanding (not yet released): release some and submit again. */
+#define SYEV3_EAGAIN 5
+
 typedef struct {
   size_t memory_budget_bytes; /* device arena for results; 0 = 16 GiB */
-  int num_streams;            /* 0 = 4 */
-  int64_t chunk;              /* matrices per launch; 0 = 2^18 */
-  int max_inflight;           /* chunks in flight per stream; 0 = 2 */
+  int64_t chunk;              /* matrices of one request per round; 0 = 2^18 */
+  int64_t round_matrices;     /* matrices per round over all requests; 0 = 2^21 */
+  int max_rounds_in_flight;   /* rounds queued on the device at once, 1..4; 0 = 2 */
 } syev3_server_config;
 
 typedef struct {
@@ -303,40 +322,56 @@ typedef struct {
   int64_t n;
   void* d_lambda;   /* device, n x 3 (valid once admitted; final when done) */
   void* d_U;        /* device, n x 9, or NULL when vectors were not asked for */
-  int64_t t_submit_ns, t_admit_ns, t_done_ns; /* host steady clock */
+  int64_t t_submit_ns, t_admit_ns, t_done_ns; /* host steady clock (admission
+                                                 and completion: the device's
+                                                 timer, mapped to it) */
 } syev3_request_info;
 
 typedef struct {
-  int64_t completed, matrices, chunks, waiting;
+  int64_t completed, matrices, chunks, waiting; /* chunks: work items issued */
   size_t arena_bytes, arena_used, arena_peak;
   int error;        /* first failure status, or SYEV3_OK */
+  int64_t rounds;   /* rounds completed on the device */
+  int64_t launches; /* kernels launched by the server */
 } syev3_server_stats;
 
 /* Creates a server on the current device; cfg may be NULL (defaults).
- * Allocates the arena with cudaMalloc: SYEV3_ECUDA if that fails. */
+ * Allocates the arena and the device queues with cudaMalloc and a mailbox
+ * in mapped host memory: SYEV3_ECUDA if that fails (nothing is kept);
+ * SYEV3_EINVAL for a budget below 256 bytes or max_rounds_in_flight > 4. */
 int syev3_server_create(const syev3_server_config* cfg, syev3_server** out);
 
-/* Stops the dispatcher, waits for work in flight, frees the arena. */
+/* Stops launching, waits for the rounds on the device, frees everything. */
 int syev3_server_destroy(syev3_server* srv);
 
 /* Queues a request: n >= 1 packed matrices at d_A (device, dtype as in
- * syev3_batched, must stay valid until the request is done).  Returns at
- * once with a ticket; SYEV3_EINVAL if the outputs could never fit the
- * arena. */
+ * syev3_batched, must stay valid and unchanged until the request is done).
+ * Returns at once with a ticket; SYEV3_EINVAL if the outputs could never fit
+ * the arena, SYEV3_EAGAIN when SYEV3_SERVER_SLOTS requests are outstanding,
+ * or the server's error after a failure. */
 int syev3_server_submit(syev3_server* srv, int dtype, const void* d_A, int64_t n, int vectors,
                         uint64_t* ticket);
 
 /* State, result pointers and timestamps of a request (non-blocking). */
 int syev3_server_query(syev3_server* srv, uint64_t ticket, syev3_request_info* info);
 
-/* Blocks until the request is done (SYEV3_OK), failed (its error) or
- * timeout_s passed (SYEV3_ETIMEOUT). */
+/* Blocks until the request is done (SYEV3_OK), failed (the server's error)
+ * or timeout_s passed (SYEV3_ETIMEOUT). */
 int syev3_server_wait(syev3_server* srv, uint64_t ticket, double timeout_s);
 
-/* Frees a done request's results (SYEV3_EINVAL if not done). */
+/* Ends a done (or failed) request: its results are freed on the device in
+ * the next round.  SYEV3_EINVAL if it is unknown or not finished.  After a
+ * failure the server keeps its device memory (its device state is not
+ * trusted) and accepts only destroy. */
 int syev3_server_release(syev3_server* srv, uint64_t ticket);
 
 int syev3_server_get_stats(syev3_server* srv, syev3_server_stats* stats);
+
+/* Failure handling, exercised without a device fault: the next round the
+ * server would launch is not launched, and the server fails as if that
+ * launch had returned `status` (not SYEV3_OK): requests not yet done fail
+ * with it, later submits return it, releases free nothing.  For tests. */
+int syev3_server_inject_failure(syev3_server* srv, int status);
 
 #ifdef __cplusplus
 }

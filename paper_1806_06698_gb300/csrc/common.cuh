@@ -45,6 +45,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
+// Plain arrival (a phase that expects no bulk bytes completes with it).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Returns true once the phase with the given parity has completed, false if
 // kWaitLimitNs went by first (timed from the first poll that found the phase
 // open; the normal path reads no timer).

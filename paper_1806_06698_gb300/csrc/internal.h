@@ -32,8 +32,9 @@ cudaError_t launch_f32(const float* A, int64_t n, float* lam, float* U, bool com
                        unsigned long long* counters, cudaStream_t stream);
 
 // Compensated FP32 with the refinement deferred to a second kernel
-// (syev3_batched_ws): the workspace holds a counter at offset 0 and, from
-// kFlagListOffset, up to n records of flagged lanes.
+// (syev3_batched_ws): the workspace holds two counters at offset 0 and, from
+// kFlagListOffset, room for n records of flagged lanes: reduced arrows from
+// the front (counter 0), the other classes from the back (counter 1).
 struct alignas(16) FlagRec {
   float v[9];       // a1 a2 b1 b2 g c s (pre-scaled arrow and rotation), mu, nu
   int code;         // e << 2 | class
@@ -44,6 +45,34 @@ constexpr size_t kFlagListOffset = 256;
 size_t f32c_workspace_bytes(int64_t n);
 cudaError_t launch_f32c_deferred(const float* A, int64_t n, float* lam, float* U, unsigned long long* counters,
                                  void* work, cudaStream_t stream);
+
+// Serving: the work of one round, built on the device by the admission
+// kernel (serve.cu) and read by the solve kernels' serving instantiations.
+// Each item is a contiguous run of one request's matrices; the items' tiles
+// of 128 matrices are numbered consecutively over the list (tile_begin is
+// the prefix sum), so a solve kernel's grid walks all requests of the round
+// as one ragged batch.
+struct ServeItem {
+  const void* A;       // first packed record of the run
+  void* lam;           // its eigenvalues
+  void* U;             // its eigenvectors, or null (eigenvalues only)
+  int64_t count;       // matrices in the run, >= 1
+  int64_t tile_begin;  // index of the run's first tile in the list
+  int64_t tag;         // the owner's reference (the serving runtime's request slot)
+};
+constexpr int kServeTile = 128;       // matrices per tile of both solve kernels
+constexpr int kServeMaxItems = 4096;  // one item per admitted request per round
+struct ServeList {
+  int64_t n_items;
+  int64_t n_tiles;
+  ServeItem items[kServeMaxItems];
+};
+
+// Solve every item of a device-resident list (grid sized from the host; the
+// kernels read the list's length on the device).
+cudaError_t launch_f64_serve(const ServeList* list, unsigned long long* counters, cudaStream_t stream);
+cudaError_t launch_f32_serve(const ServeList* list, bool compensated, unsigned long long* counters,
+                             cudaStream_t stream);
 
 template <class T>
 cudaError_t launch_bwd(const T* lam, const T* U, const T* gl, const T* gU, int64_t n, T* gA, T tau,

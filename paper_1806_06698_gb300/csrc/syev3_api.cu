@@ -65,7 +65,7 @@ int syev3::record_cuda_error(cudaError_t e) {
 
 extern "C" {
 
-int syev3_abi_version(void) { return 1; }
+int syev3_abi_version(void) { return 2; }
 
 const char* syev3_status_string(int status) {
   switch (status) {
@@ -74,6 +74,7 @@ const char* syev3_status_string(int status) {
     case SYEV3_ECUDA: return "SYEV3_ECUDA: CUDA call failed";
     case SYEV3_ENOCONV: return "SYEV3_ENOCONV: zero finder hit its step cap";
     case SYEV3_ETIMEOUT: return "SYEV3_ETIMEOUT: a device-side wait ran out";
+    case SYEV3_EAGAIN: return "SYEV3_EAGAIN: the server's request ring is full";
     default: return "SYEV3: unknown status";
   }
 }

@@ -35,15 +35,46 @@ __host__ __device__ constexpr int tile_of() {
 
 __device__ unsigned g_flags_bwd;
 
+// Helpers with an FP64 form that keeps compares and exact scalings by 2 off
+// the FP64 pipe (the one that bounds the FP64 backward): compares of
+// non-negative values as bit patterns, halving and doubling by exponent
+// arithmetic.  Both forms return bit-identical values to the plain
+// expressions 0.5 / x (from a <= 1 ulp reciprocal in FP64), a < b and 2 x.
+
+// 1 / (2 x), x != 0.
 template <class T>
-__device__ __forceinline__ T recip(T x);
+__device__ __forceinline__ T half_recip(T x);
 template <>
-__device__ __forceinline__ double recip<double>(double x) {
-  return (fabs(x) >= 0x1p-1000 && fabs(x) <= 0x1p+1000) ? rcp64(x) : 1.0 / x;
+__device__ __forceinline__ double half_recip<double>(double x) {
+  if (hi_mag(x) >= hi_pow2(-1000) && hi_mag(x) <= hi_pow2(1000)) {  // |x| in [2^-1000, 2^1000]
+    const double r = rcp64(x);  // normal, far from both ends of the range
+    return __hiloint2double(__double2hiint(r) - (1 << 20), __double2loint(r));
+  }
+  return 0.5 / x;
 }
 template <>
-__device__ __forceinline__ float recip<float>(float x) {
-  return 1.0f / x;
+__device__ __forceinline__ float half_recip<float>(float x) {
+  return 0.5f / x;
+}
+
+// a < b for a, b >= +0 (not NaN).
+template <class T>
+__device__ __forceinline__ bool lt_nonneg(T a, T b) {
+  return a < b;
+}
+template <>
+__device__ __forceinline__ bool lt_nonneg<double>(double a, double b) {
+  return dbits(a) < dbits(b);
+}
+
+// 2 x, exactly.
+template <class T>
+__device__ __forceinline__ T twice(T x) {
+  return T(2) * x;
+}
+template <>
+__device__ __forceinline__ double twice<double>(double x) {
+  return mul_pow2(x, 1);
 }
 
 // Packed gradient of one matrix.  l[3] ascending eigenvalues, U[9] row-major
@@ -67,9 +98,9 @@ __device__ __forceinline__ void grad_one(const T l[3], const T U[9], const T gl[
     // |gap| < tau ||lambda||_2, compared squared (no square root).
     const T thr2 = (tau * tau) * fma(l[0], l[0], fma(l[1], l[1], l[2] * l[2]));
     const T gap01 = l[1] - l[0], gap02 = l[2] - l[0], gap12 = l[2] - l[1];
-    c01 = (gap01 * gap01 < thr2) ? T(0) : T(0.5) * d01 * recip(gap01);
-    c02 = (gap02 * gap02 < thr2) ? T(0) : T(0.5) * d02 * recip(gap02);
-    c12 = (gap12 * gap12 < thr2) ? T(0) : T(0.5) * d12 * recip(gap12);
+    c01 = lt_nonneg(gap01 * gap01, thr2) ? T(0) : d01 * half_recip(gap01);
+    c02 = lt_nonneg(gap02 * gap02, thr2) ? T(0) : d02 * half_recip(gap02);
+    c12 = lt_nonneg(gap12 * gap12, thr2) ? T(0) : d12 * half_recip(gap12);
   }
   const T C[3][3] = {{gl[0], c01, c02}, {c01, gl[1], c12}, {c02, c12, gl[2]}};
   // P = U sym(C); S = P U^T (upper triangle).
@@ -85,9 +116,9 @@ __device__ __forceinline__ void grad_one(const T l[3], const T U[9], const T gl[
   out[0] = S(0, 0);
   out[1] = S(1, 1);
   out[2] = S(2, 2);
-  out[3] = T(2) * S(0, 1);
-  out[4] = T(2) * S(0, 2);
-  out[5] = T(2) * S(1, 2);
+  out[3] = twice(S(0, 1));
+  out[4] = twice(S(0, 2));
+  out[5] = twice(S(1, 2));
 }
 
 // Stage `count` elements of T from global memory into shared memory: a bulk

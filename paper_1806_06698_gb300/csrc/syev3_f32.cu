@@ -35,6 +35,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "serve_tile.cuh"
 #include "solve_f64.cuh"
 
 namespace syev3 {
@@ -46,8 +47,17 @@ constexpr float kEps32 = 0x1p-23f;
 constexpr float kCDefl32 = 1.0f;          // C of the deflation test (Sec. 1.1)
 constexpr float kCTerm32 = 2.0f;          // C of the stopping rule (Sec. 1.4.1)
 constexpr float kTinySpike32 = 0x1p-60f;  // spikes below this are zeroed (beta-deflation)
-constexpr float kNearDefl = 16.0f;        // near-deflated: test sides within this factor
-constexpr float kClusterTau = 0x1p-16f;   // clustered: relative gap below this
+// The lanes refined in FP64 are those FP32 cannot resolve: a deflation test
+// whose two sides lie within a factor kNearDefl of each other (the decision
+// rests on the last bits of the FP32 data), or a relative eigenvalue gap
+// below kClusterTau = one unit of FP32 resolution (the pair's eigenvectors are
+// then not determined by FP32 arithmetic).  A sweep of both on the mixed and
+// structure-tensor batches found every subset's error against the FP64
+// oracle within 2.1 eps32 ||A||_F (eigenvalues), 2.9 (residual) and 7.6
+// (orthogonality) for every setting, far inside the 64 eps32 bar; wider
+// windows only cost time (a factor 16 window flagged 16 % of the mixed batch).
+constexpr float kNearDefl = 2.0f;         // near-deflated: test sides within this factor
+constexpr float kClusterTau = 0x1p-23f;   // clustered: relative gap below this
 constexpr double kResidualTol = 16.0 * 0x1p-23;  // FP64 residual check, times ||A||_F
 constexpr int kPlain = 0, kInline = 1, kDeferred = 2;  // modes of k_syev3_f32
 
@@ -464,12 +474,21 @@ __device__ __forceinline__ bool refine_one(const float f[9], const int code, con
 // syev3_batched_ws -- and refined by k_refine_f32; the kernel then holds no
 // FP64 code and needs fewer registers).
 // kVectors = false (plain mode only): eigenvalues only, U_out NULL.
-template <bool kBulkIn, int kMode, bool kVectors = true>
+// kServe: the serving build (plain or in-kernel compensated).  The tiles are
+// those of the device-resident work list `list` (A, n, lam_out and U_out are
+// unused), each with its own input and output rows; a tile's input is
+// bulk-copied from its first 16-byte boundary-aligned record on, or loaded
+// with plain loads when its start is not 16-byte aligned.  The production
+// builds (kServe = false) compile this out.
+template <bool kBulkIn, int kMode, bool kVectors = true, bool kServe = false>
 __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A, int64_t n,
                                                     float* __restrict__ lam_out, float* __restrict__ U_out,
                                                     unsigned long long* __restrict__ counters,
                                                     FlagRec* __restrict__ flag_list,
-                                                    unsigned long long* __restrict__ flag_count) {
+                                                    unsigned long long* __restrict__ flag_count,
+                                                    const ServeList* __restrict__ list) {
+  static_assert(!kServe || (kBulkIn && kMode != kDeferred && kVectors), "the serving build is bulk, vectors");
+  static_assert(kTPB == kServeTile, "serving tiles are solve tiles");
   constexpr bool kComp = kMode != kPlain;
   constexpr bool kDefer = kMode == kDeferred;
   __shared__ alignas(16) float s_in[2][kTPB * 6];
@@ -490,13 +509,18 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
   __shared__ bool s_more_capped[2 * kTPB];
   __shared__ int s_nmore;
   __shared__ alignas(8) uint64_t s_bar[2];
+  // Serving build: the tile of each buffer; the eigenvector row of each
+  // flagged lane in the list (s_fg then holds its eigenvalue row's address).
+  __shared__ TileRef<float> s_ref[kServe ? 2 : 1];
+  __shared__ float* s_fU[(kServe && kInl) ? kFW : 1];
 
   const int tid = threadIdx.x, lane_id = tid & 31;
   const unsigned lt_mask = (1u << lane_id) - 1u;
-  const int64_t n_tiles = (n + kTPB - 1) / kTPB;
-  const bool want_U = (U_out != nullptr);
-  const bool vec_lam = ((reinterpret_cast<uintptr_t>(lam_out) & 15) == 0);
-  const bool vec_U = want_U && ((reinterpret_cast<uintptr_t>(U_out) & 15) == 0);
+  const int64_t n_tiles = kServe ? list->n_tiles : (n + kTPB - 1) / kTPB;
+  bool want_U = (U_out != nullptr);
+  bool vec_lam = ((reinterpret_cast<uintptr_t>(lam_out) & 15) == 0);
+  bool vec_U = want_U && ((reinterpret_cast<uintptr_t>(U_out) & 15) == 0);
+  int64_t cursor = 0;  // serving build: item cursor of the tiles this CTA issues (thread 0)
 
   if (tid == 0) {
     s_nflag = 0;
@@ -513,6 +537,18 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
   // record of a tile with an odd count (8 bytes past a 16-byte boundary) is
   // loaded with plain loads after the wait.
   auto issue = [&](int64_t tile, int buf) {
+    if constexpr (kServe) {
+      const TileRef<float> r = serve_tile<float>(list, tile, cursor);
+      s_ref[buf] = r;
+      const uint32_t bytes = (reinterpret_cast<uintptr_t>(r.src) & 15) ? 0u : (((uint32_t)r.cnt * 24u) & ~15u);
+      if (bytes == 0) {  // plain loads after the wait
+        mbar_arrive(&s_bar[buf]);
+        return;
+      }
+      mbar_arrive_expect_tx(&s_bar[buf], bytes);
+      bulk_g2s(s_in[buf], r.src, bytes, &s_bar[buf]);
+      return;
+    }
     const int64_t base = tile * kTPB;
     const int cnt = (int)((n - base) < kTPB ? (n - base) : kTPB);
     const uint32_t bytes = ((uint32_t)cnt * 24u) & ~15u;
@@ -528,7 +564,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
 
   for (; tile < n_tiles; tile += gridDim.x, buf ^= 1) {
     const int64_t base = tile * kTPB;
-    const int cnt = (int)((n - base) < kTPB ? (n - base) : kTPB);
+    int cnt = (int)((n - base) < kTPB ? (n - base) : kTPB);
     const int64_t next = tile + gridDim.x;
     if (kBulkIn) {
       if (tid == 0 && next < n_tiles) issue(next, buf ^ 1);
@@ -540,9 +576,21 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
         return;
       }
       phases ^= 1u << buf;
-      const int done_f = (int)((((uint32_t)cnt * 24u) & ~15u) / 4u);
-      for (int i = done_f + tid; i < cnt * 6; i += kTPB) s_in[buf][i] = A[base * 6 + i];
-      if (done_f < cnt * 6) __syncthreads();
+      if constexpr (kServe) {
+        const TileRef<float> r = s_ref[buf];
+        cnt = r.cnt;
+        want_U = (r.U != nullptr);
+        vec_lam = ((reinterpret_cast<uintptr_t>(r.lam) & 15) == 0);
+        vec_U = want_U && ((reinterpret_cast<uintptr_t>(r.U) & 15) == 0);
+        const int done_f =
+            (reinterpret_cast<uintptr_t>(r.src) & 15) ? 0 : (int)((((uint32_t)cnt * 24u) & ~15u) / 4u);
+        for (int i = done_f + tid; i < cnt * 6; i += kTPB) s_in[buf][i] = r.src[i];
+        if (done_f < cnt * 6) __syncthreads();
+      } else {
+        const int done_f = (int)((((uint32_t)cnt * 24u) & ~15u) / 4u);
+        for (int i = done_f + tid; i < cnt * 6; i += kTPB) s_in[buf][i] = A[base * 6 + i];
+        if (done_f < cnt * 6) __syncthreads();
+      }
     } else {
       for (int i = tid; i < cnt * 6; i += kTPB) s_in[buf][i] = A[base * 6 + i];
       __syncthreads();
@@ -665,19 +713,28 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
     }
 
     if (kDefer) {
-      // Append the flagged lanes to the global list (one atomic per warp);
-      // k_refine_f32 refines them and overwrites their outputs.
-      const unsigned m = __ballot_sync(0xffffffffu, flagged);
-      unsigned long long wbase = 0;
-      if (lane_id == 0 && m) wbase = atomicAdd(flag_count, (unsigned long long)__popc(m));
-      wbase = __shfl_sync(0xffffffffu, wbase, 0);
+      // Append the flagged lanes to the global list (one atomic per warp and
+      // class): reduced arrows from the front (count [0]), the other classes
+      // from the back (count [1]), so that k_refine_f32 runs each class in
+      // whole warps; it refines them and overwrites their outputs.
+      const bool fr = flagged && L.cls == kRed;
+      const unsigned mr = __ballot_sync(0xffffffffu, fr);
+      const unsigned mo = __ballot_sync(0xffffffffu, flagged && !fr);
+      unsigned long long br = 0, bo = 0;
+      if (lane_id == 0) {
+        if (mr) br = atomicAdd(&flag_count[0], (unsigned long long)__popc(mr));
+        if (mo) bo = atomicAdd(&flag_count[1], (unsigned long long)__popc(mo));
+      }
+      br = __shfl_sync(0xffffffffu, br, 0);
+      bo = __shfl_sync(0xffffffffu, bo, 0);
       if (flagged) {
         FlagRec r;
         r.v[0] = L.a1; r.v[1] = L.a2; r.v[2] = L.b1; r.v[3] = L.b2; r.v[4] = L.g; r.v[5] = L.c; r.v[6] = L.s;
         r.v[7] = root[0]; r.v[8] = root[1];
         r.code = (L.e << 2) | L.cls;
         r.gidx = base + tid;
-        flag_list[wbase + __popc(m & lt_mask)] = r;
+        const int64_t at = fr ? (int64_t)(br + __popc(mr & lt_mask)) : n - 1 - (int64_t)(bo + __popc(mo & lt_mask));
+        flag_list[at] = r;
       }
     } else if (kComp) {
       // Compact the flagged lanes after the carried ones and refine a whole
@@ -699,7 +756,13 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
 #pragma unroll
         for (int k = 0; k < 6; ++k) f[9 + k] = a_in[k];
         s_fc[slot] = (L.e << 2) | L.cls;
-        s_fg[slot] = base + tid;
+        if constexpr (kServe) {
+          const TileRef<float> r = s_ref[buf];
+          s_fg[slot] = (int64_t)reinterpret_cast<uintptr_t>(r.lam + tid * 3);
+          s_fU[slot] = r.U ? r.U + tid * 9 : nullptr;
+        } else {
+          s_fg[slot] = base + tid;
+        }
       }
       __syncthreads();
       const int n_avail = nfc + s_nflag;
@@ -710,13 +773,25 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
         const bool bad = refine_one(&s_fa[i * kFA], s_fc[i], counters != nullptr ? &s_fa[i * kFA + 9] : nullptr,
                                     lam, U);
         if (bad) atomicAdd(&counters[3], 1ull);
-        const int64_t gi = s_fg[i], row = gi - base;
+        const int64_t gi = s_fg[i];
+        int64_t row;
+        float *dl_far, *dU_far;  // where a lane of an earlier tile writes
+        if constexpr (kServe) {
+          const int64_t d = (int64_t)(uintptr_t)gi - (int64_t)reinterpret_cast<uintptr_t>(s_ref[buf].lam);
+          row = (d >= 0 && d < (int64_t)cnt * 12) ? d / 12 : -1;
+          dl_far = reinterpret_cast<float*>((uintptr_t)gi);
+          dU_far = s_fU[i];
+        } else {
+          row = gi - base;
+          dl_far = lam_out + gi * 3;
+          dU_far = want_U ? U_out + gi * 9 : nullptr;
+        }
         const bool here = row >= 0 && row < cnt;
-        float* dl = here ? &s_lam[row * 3] : lam_out + gi * 3;
+        float* dl = here ? &s_lam[row * 3] : dl_far;
 #pragma unroll
         for (int k = 0; k < 3; ++k) dl[k] = (float)lam[k];
-        if (here || want_U) {
-          float* dU = here ? &s_U[row * 9] : U_out + gi * 9;
+        if (here || dU_far != nullptr) {
+          float* dU = here ? &s_U[row * 9] : dU_far;
 #pragma unroll
           for (int k = 0; k < 9; ++k) dU[k] = (float)U[k];
         }
@@ -728,6 +803,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
         for (int k = 0; k < kFA; ++k) s_fa[tid * kFA + k] = s_fa[(P + tid) * kFA + k];
         s_fc[tid] = s_fc[P + tid];
         s_fg[tid] = s_fg[P + tid];
+        if constexpr (kServe) s_fU[tid] = s_fU[P + tid];
       }
       nfc = nc_next;
     }
@@ -748,7 +824,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
     }
 
     {
-      float* dst = lam_out + base * 3;
+      float* dst = kServe ? s_ref[buf].lam : lam_out + base * 3;
       const int m = cnt * 3;
       if (vec_lam) {
         float4* d4 = reinterpret_cast<float4*>(dst);
@@ -760,7 +836,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
       }
     }
     if (want_U) {
-      float* dst = U_out + base * 9;
+      float* dst = kServe ? s_ref[buf].U : U_out + base * 9;
       const int m = cnt * 9;
       if (vec_U) {
         float4* d4 = reinterpret_cast<float4*>(dst);
@@ -782,22 +858,25 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
                                   lam, U);
       if (bad) atomicAdd(&counters[3], 1ull);
       const int64_t gi = s_fg[i];
+      float* dl = kServe ? reinterpret_cast<float*>((uintptr_t)gi) : lam_out + gi * 3;
+      float* dU = kServe ? s_fU[kServe ? i : 0] : (want_U ? U_out + gi * 9 : nullptr);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) lam_out[gi * 3 + k] = (float)lam[k];
-      if (want_U) {
+      for (int k = 0; k < 3; ++k) dl[k] = (float)lam[k];
+      if (dU != nullptr) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) U_out[gi * 9 + k] = (float)U[k];
+        for (int k = 0; k < 9; ++k) dU[k] = (float)U[k];
       }
     }
   }
 }
 
-template <bool kBulkIn, int kMode, bool kVectors>
+template <bool kBulkIn, int kMode, bool kVectors, bool kServe = false>
 int blocks_per_sm_f32() {
   static int cached = -1;
   if (cached < 0) {
     int v = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_syev3_f32<kBulkIn, kMode, kVectors>, kTPB, 0);
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_syev3_f32<kBulkIn, kMode, kVectors, kServe>, kTPB, 0);
     cached = (e == cudaSuccess && v > 0) ? v : 1;
   }
   return cached;
@@ -809,23 +888,36 @@ cudaError_t launch(const float* A, int64_t n, float* lam, float* U, unsigned lon
   const int64_t n_tiles = (n + kTPB - 1) / kTPB;
   const int64_t resident = (int64_t)sms * blocks_per_sm_f32<kBulkIn, kMode, kVectors>();
   const int grid = (int)(n_tiles < resident ? n_tiles : resident);
-  k_syev3_f32<kBulkIn, kMode, kVectors><<<grid, kTPB, 0, stream>>>(A, n, lam, U, counters, flag_list, flag_count);
+  k_syev3_f32<kBulkIn, kMode, kVectors>
+      <<<grid, kTPB, 0, stream>>>(A, n, lam, U, counters, flag_list, flag_count, nullptr);
+  return cudaGetLastError();
+}
+
+template <int kMode>
+cudaError_t launch_serve(const ServeList* list, unsigned long long* counters, cudaStream_t stream, int sms) {
+  // The list's length is known only on the device: a resident grid; CTAs
+  // without a tile exit at once.
+  const int grid = sms * blocks_per_sm_f32<true, kMode, true, true>();
+  k_syev3_f32<true, kMode, true, true>
+      <<<grid, kTPB, 0, stream>>>(nullptr, 0, nullptr, nullptr, counters, nullptr, nullptr, list);
   return cudaGetLastError();
 }
 
 // The refinement of the deferred compensated form: one flagged lane per
-// thread, grid-stride over the list (its length is read on the device).
+// thread, grid-stride over the list (its lengths are read on the device):
+// first the reduced arrows (list front), then the other classes (list back,
+// n records from the front), so each warp but one runs a single class.
 constexpr int kRefineTPB = 128;
 
 __global__ void __launch_bounds__(kRefineTPB) k_refine_f32(const FlagRec* __restrict__ list,
                                                            const unsigned long long* __restrict__ count,
-                                                           const float* __restrict__ A, float* __restrict__ lam_out,
-                                                           float* __restrict__ U_out,
+                                                           int64_t n, const float* __restrict__ A,
+                                                           float* __restrict__ lam_out, float* __restrict__ U_out,
                                                            unsigned long long* __restrict__ counters) {
-  const unsigned long long m = *count;
+  const unsigned long long m_red = count[0], m = m_red + count[1];
   for (unsigned long long i = (unsigned long long)blockIdx.x * kRefineTPB + threadIdx.x; i < m;
        i += (unsigned long long)gridDim.x * kRefineTPB) {
-    const FlagRec r = list[i];
+    const FlagRec r = list[i < m_red ? (int64_t)i : n - 1 - (int64_t)(i - m_red)];
     double lam[3], U[9];
     const bool bad = refine_one(r.v, r.code, counters != nullptr ? A + r.gidx * 6 : nullptr, lam, U);
     if (bad) atomicAdd(&counters[3], 1ull);
@@ -868,6 +960,17 @@ cudaError_t launch_f32(const float* A, int64_t n, float* lam, float* U, bool com
                      : launch<false, kPlain>(A, n, lam, U, counters, nullptr, nullptr, stream, sms);
 }
 
+cudaError_t launch_f32_serve(const ServeList* list, bool compensated, unsigned long long* counters,
+                             cudaStream_t stream) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  return compensated ? launch_serve<kInline>(list, counters, stream, sms)
+                     : launch_serve<kPlain>(list, counters, stream, sms);
+}
+
 size_t f32c_workspace_bytes(int64_t n) { return kFlagListOffset + (size_t)n * sizeof(FlagRec); }
 
 cudaError_t launch_f32c_deferred(const float* A, int64_t n, float* lam, float* U, unsigned long long* counters,
@@ -880,13 +983,13 @@ cudaError_t launch_f32c_deferred(const float* A, int64_t n, float* lam, float* U
   if (e != cudaSuccess) return e;
   auto* count = static_cast<unsigned long long*>(work);
   auto* list = reinterpret_cast<FlagRec*>(static_cast<char*>(work) + kFlagListOffset);
-  e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), stream);
+  e = cudaMemsetAsync(count, 0, 2 * sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
   e = ((reinterpret_cast<uintptr_t>(A) & 15) == 0)
           ? launch<true, kDeferred>(A, n, lam, U, counters, list, count, stream, sms)
           : launch<false, kDeferred>(A, n, lam, U, counters, list, count, stream, sms);
   if (e != cudaSuccess) return e;
-  k_refine_f32<<<sms * refine_blocks_per_sm(), kRefineTPB, 0, stream>>>(list, count, A, lam, U, counters);
+  k_refine_f32<<<sms * refine_blocks_per_sm(), kRefineTPB, 0, stream>>>(list, count, n, A, lam, U, counters);
   return cudaGetLastError();
 }
 

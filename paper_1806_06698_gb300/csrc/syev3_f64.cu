@@ -25,6 +25,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "serve_tile.cuh"
 #include "solve_f64.cuh"
 
 namespace syev3 {
@@ -46,10 +47,18 @@ __device__ unsigned g_flags;     // kFlagWaitTimeout when a bulk-copy wait ran o
 // has these switches compiled out.
 // kVectors = false: eigenvalues only (U_out is NULL); the eigenvectors are
 // not formed.
-template <bool kBulkIn, bool kStudy, bool kVectors>
+// kServe: the serving build.  The tiles are those of the device-resident
+// work list `list` (A, n, lam_out and U_out are unused): runs of matrices of
+// many requests, each tile with its own input and output rows, solved as one
+// ragged batch.  A tile whose input is not 16-byte aligned is loaded with
+// plain loads.  The production build (kServe = false) compiles this out.
+template <bool kBulkIn, bool kStudy, bool kVectors, bool kServe = false>
 __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A, int64_t n,
                                                     double* __restrict__ lam_out, double* __restrict__ U_out,
-                                                    unsigned long long* __restrict__ counters, Method method) {
+                                                    unsigned long long* __restrict__ counters, Method method,
+                                                    const ServeList* __restrict__ list) {
+  static_assert(!kServe || (kBulkIn && !kStudy && kVectors), "the serving build is bulk, production, vectors");
+  static_assert(kTPB == kServeTile, "serving tiles are solve tiles");
   const int zf = kStudy ? method.zero_finder : kZfProduction;
   const bool eispack = kStudy && method.deflation_test == kDeflEispack;
   __shared__ alignas(16) double s_in[2][kTPB * 6];
@@ -77,13 +86,20 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
   __shared__ int s_oth[kTPB];
   __shared__ int s_nred, s_noth;
   __shared__ alignas(8) uint64_t s_bar[2];
+  // Serving build: the tile of each buffer, and the eigenvector row of each
+  // reduced arrow in W and in the carry (s_wg and s_cg then hold the
+  // eigenvalue row's address instead of a batch index).
+  __shared__ TileRef<double> s_ref[kServe ? 2 : 1];
+  __shared__ double* s_wU[kServe ? kW : 1];
+  __shared__ double* s_cU[kServe ? 32 : 1];
 
   const int tid = threadIdx.x, lane_id = tid & 31;
   const unsigned lt_mask = (1u << lane_id) - 1u;
-  const int64_t n_tiles = (n + kTPB - 1) / kTPB;
-  const bool want_U = (U_out != nullptr);
-  const bool vec_lam = ((reinterpret_cast<uintptr_t>(lam_out) & 15) == 0);
-  const bool vec_U = want_U && ((reinterpret_cast<uintptr_t>(U_out) & 15) == 0);
+  const int64_t n_tiles = kServe ? list->n_tiles : (n + kTPB - 1) / kTPB;
+  bool want_U = (U_out != nullptr);
+  bool vec_lam = ((reinterpret_cast<uintptr_t>(lam_out) & 15) == 0);
+  bool vec_U = want_U && ((reinterpret_cast<uintptr_t>(U_out) & 15) == 0);
+  int64_t cursor = 0;  // serving build: item cursor of the tiles this CTA issues (thread 0)
 
   if (tid == 0) {
     s_nhard = 0;
@@ -98,6 +114,18 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
   __syncthreads();
 
   auto issue = [&](int64_t tile, int buf) {
+    if constexpr (kServe) {
+      const TileRef<double> r = serve_tile<double>(list, tile, cursor);
+      s_ref[buf] = r;
+      if (reinterpret_cast<uintptr_t>(r.src) & 15) {  // plain loads after the wait
+        mbar_arrive(&s_bar[buf]);
+        return;
+      }
+      const uint32_t bytes = (uint32_t)r.cnt * 48u;
+      mbar_arrive_expect_tx(&s_bar[buf], bytes);
+      bulk_g2s(s_in[buf], r.src, bytes, &s_bar[buf]);
+      return;
+    }
     const int64_t base = tile * kTPB;
     const int cnt = (int)((n - base) < kTPB ? (n - base) : kTPB);
     const uint32_t bytes = (uint32_t)cnt * 48u;  // 48 = 3 * 16: always a multiple of 16
@@ -122,7 +150,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
     const bool flush = (tile >= n_tiles);  // the pass that finishes the carry
     if (flush && nc == 0) break;
     const int64_t base = tile * kTPB;
-    const int cnt = flush ? 0 : (int)((n - base) < kTPB ? (n - base) : kTPB);
+    int cnt = flush ? 0 : (int)((n - base) < kTPB ? (n - base) : kTPB);
     const int64_t next = tile + gridDim.x;
     if (!flush) {
       if (kBulkIn) {
@@ -138,6 +166,17 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
           return;
         }
         phases ^= 1u << buf;
+        if constexpr (kServe) {
+          const TileRef<double> r = s_ref[buf];
+          cnt = r.cnt;
+          want_U = (r.U != nullptr);
+          vec_lam = ((reinterpret_cast<uintptr_t>(r.lam) & 15) == 0);
+          vec_U = want_U && ((reinterpret_cast<uintptr_t>(r.U) & 15) == 0);
+          if (reinterpret_cast<uintptr_t>(r.src) & 15) {
+            for (int i = tid; i < cnt * 6; i += kTPB) s_in[buf][i] = r.src[i];
+            __syncthreads();
+          }
+        }
       } else {
         for (int i = tid; i < cnt * 6; i += kTPB) s_in[buf][i] = A[base * 6 + i];
         __syncthreads();
@@ -152,6 +191,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
       for (int f = 0; f < 7; ++f) s_w[f * kW + tid] = s_ca[f][tid];
       s_we[tid] = s_ce[tid];
       s_wg[tid] = s_cg[tid];
+      if constexpr (kServe) s_wU[tid] = s_cU[tid];
     }
     {
       Lane A0;
@@ -178,7 +218,13 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
         s_w[5 * kW + slot] = A0.c;
         s_w[6 * kW + slot] = A0.s;
         s_we[slot] = A0.e;
-        s_wg[slot] = base + tid;
+        if constexpr (kServe) {
+          const TileRef<double> r = s_ref[buf];
+          s_wg[slot] = (int64_t)reinterpret_cast<uintptr_t>(r.lam + tid * 3);
+          s_wU[slot] = r.U ? r.U + tid * 9 : nullptr;
+        } else {
+          s_wg[slot] = base + tid;
+        }
       }
       if (oth) s_oth[ob + __popc(mo & lt_mask)] = tid;
       if (kStudy && counters != nullptr) {
@@ -201,10 +247,12 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
       for (int f = 0; f < 7; ++f) s_ca[f][tid] = s_w[f * kW + P + tid];
       s_ce[tid] = s_we[P + tid];
       s_cg[tid] = s_wg[P + tid];
+      if constexpr (kServe) s_cU[tid] = s_wU[P + tid];
     }
     Lane L;
     L.cls = kIdle;
     int64_t gidx = -1;
+    double* urow = nullptr;  // serving build: the arrow's eigenvector row (null: none wanted)
     if (tid < P) {
       L.a1 = s_w[0 * kW + tid];
       L.a2 = s_w[1 * kW + tid];
@@ -216,6 +264,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
       L.e = s_we[tid];
       L.cls = kReduced;
       gidx = s_wg[tid];
+      if constexpr (kServe) urow = s_wU[tid];
     }
 
     // Phases B, C: FP32 seeds, then one FP64 step and the stopping test.
@@ -347,12 +396,28 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
     } else if (reduced) {
       double lam[3], U[9];
       finish_lane(L, root[0], root[1], lam, U);
-      const int64_t row = gidx - base;
+      int64_t row;
+      if constexpr (kServe) {
+        // Byte offset of the arrow's eigenvalue row from this tile's first row.
+        const int64_t d = flush ? -1
+                                : (int64_t)(uintptr_t)gidx - (int64_t)reinterpret_cast<uintptr_t>(s_ref[buf].lam);
+        row = (d >= 0 && d < (int64_t)cnt * 24) ? d / 24 : -1;
+      } else {
+        row = gidx - base;
+      }
       if (row >= 0 && row < cnt) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) s_lam[row * 3 + k] = lam[k];
 #pragma unroll
         for (int k = 0; k < 9; ++k) s_U[row * 9 + k] = U[k];
+      } else if constexpr (kServe) {
+        double* lrow = reinterpret_cast<double*>((uintptr_t)gidx);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) lrow[k] = lam[k];
+        if (urow != nullptr) {
+#pragma unroll
+          for (int k = 0; k < 9; ++k) urow[k] = U[k];
+        }
       } else {
 #pragma unroll
         for (int k = 0; k < 3; ++k) lam_out[gidx * 3 + k] = lam[k];
@@ -404,7 +469,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
     // Coalesced write-back of the tile: 16-byte stores where aligned.  The
     // rows of arrows carried to the next pass receive their results then.
     if (!flush) {
-      double* dst = lam_out + base * 3;
+      double* dst = kServe ? s_ref[buf].lam : lam_out + base * 3;
       const int m = cnt * 3;
       if (vec_lam) {
         double2* d2 = reinterpret_cast<double2*>(dst);
@@ -416,7 +481,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
       }
     }
     if (!flush && want_U) {
-      double* dst = U_out + base * 9;
+      double* dst = kServe ? s_ref[buf].U : U_out + base * 9;
       const int m = cnt * 9;
       if (vec_U) {
         double2* d2 = reinterpret_cast<double2*>(dst);
@@ -433,13 +498,13 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
   }
 }
 
-template <bool kBulkIn, bool kStudy, bool kVectors>
+template <bool kBulkIn, bool kStudy, bool kVectors, bool kServe = false>
 int blocks_per_sm_f64() {
   static int cached = -1;
   if (cached < 0) {
     int v = 0;
-    const cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_syev3_f64<kBulkIn, kStudy, kVectors>, kTPB, 0);
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &v, k_syev3_f64<kBulkIn, kStudy, kVectors, kServe>, kTPB, 0);
     cached = (e == cudaSuccess && v > 0) ? v : 1;
   }
   return cached;
@@ -456,11 +521,25 @@ cudaError_t launch_f64_t(const double* A, int64_t n, double* lam, double* U, uns
   const int64_t n_tiles = (n + kTPB - 1) / kTPB;
   const int64_t resident = (int64_t)sms * blocks_per_sm_f64<kBulkIn, kStudy, kVectors>();
   const int grid = (int)(n_tiles < resident ? n_tiles : resident);
-  k_syev3_f64<kBulkIn, kStudy, kVectors><<<grid, kTPB, 0, stream>>>(A, n, lam, U, counters, method);
+  k_syev3_f64<kBulkIn, kStudy, kVectors><<<grid, kTPB, 0, stream>>>(A, n, lam, U, counters, method, nullptr);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t launch_f64_serve(const ServeList* list, unsigned long long* counters, cudaStream_t stream) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  // The list's length is known only on the device: a resident grid; CTAs
+  // without a tile exit at once.
+  const int grid = sms * blocks_per_sm_f64<true, false, true, true>();
+  const Method m{kZfProduction, kDeflSimplified};
+  k_syev3_f64<true, false, true, true><<<grid, kTPB, 0, stream>>>(nullptr, 0, nullptr, nullptr, counters, m, list);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_f64(const double* A, int64_t n, double* lam, double* U, unsigned long long* counters,
                        cudaStream_t stream) {

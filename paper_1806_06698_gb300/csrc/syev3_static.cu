@@ -14,7 +14,10 @@
 // (other streams, other host threads) race on it and must be ordered by the
 // caller.  The first call on a device resolves the array's address with
 // cudaGetSymbolAddress (which may load the module); it must happen before
-// any stream capture begins on that device.
+// any stream capture begins on that device.  The address is cached per
+// device index for the life of the process, so the entry point must not be
+// used on a device after cudaDeviceReset (a new context may load the module
+// at another address).
 
 #include <cstdint>
 #include <mutex>
@@ -29,7 +32,7 @@ namespace {
 constexpr int64_t kStaticMaxN = SYEV3_STATIC_MAX_N;
 constexpr size_t kStaticBytes = syev3::kFlagListOffset + (size_t)kStaticMaxN * sizeof(syev3::FlagRec);
 
-// Counter at offset 0, the list of flagged lanes from kFlagListOffset.
+// Two counters at offset 0, the list of flagged lanes from kFlagListOffset.
 static __device__ __align__(256) unsigned char g_static_ws[kStaticBytes];
 
 constexpr int kMaxDevices = 64;

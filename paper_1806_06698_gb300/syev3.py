@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsyev3.so")
 
 SYEV3_F64, SYEV3_F32, SYEV3_F32_COMPENSATED = 0, 1, 2
-SYEV3_OK, SYEV3_EINVAL, SYEV3_ECUDA, SYEV3_ENOCONV, SYEV3_ETIMEOUT = 0, 1, 2, 3, 4
+SYEV3_OK, SYEV3_EINVAL, SYEV3_ECUDA, SYEV3_ENOCONV, SYEV3_ETIMEOUT, SYEV3_EAGAIN = 0, 1, 2, 3, 4, 5
 NUM_COUNTERS = 4
 # syev3_batched_method: variants of the zero finder and the deflation test,
 # and the layout of its statistics (include/syev3.h).
@@ -294,8 +294,8 @@ def eigh3(A6: torch.Tensor, compensated: bool = False, gap_tau: float = 1e-6):
 
 
 class _ServerConfig(ctypes.Structure):
-    _fields_ = [("memory_budget_bytes", ctypes.c_size_t), ("num_streams", ctypes.c_int),
-                ("chunk", ctypes.c_int64), ("max_inflight", ctypes.c_int)]
+    _fields_ = [("memory_budget_bytes", ctypes.c_size_t), ("chunk", ctypes.c_int64),
+                ("round_matrices", ctypes.c_int64), ("max_rounds_in_flight", ctypes.c_int)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -307,7 +307,12 @@ class RequestInfo(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("matrices", ctypes.c_int64), ("chunks", ctypes.c_int64),
                 ("waiting", ctypes.c_int64), ("arena_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t),
-                ("arena_peak", ctypes.c_size_t), ("error", ctypes.c_int)]
+                ("arena_peak", ctypes.c_size_t), ("error", ctypes.c_int), ("rounds", ctypes.c_int64),
+                ("launches", ctypes.c_int64)]
+
+
+# Requests outstanding (submitted, not released) at most (include/syev3.h).
+SERVER_SLOTS = 4096
 
 
 def _bind_server(lib):
@@ -322,22 +327,23 @@ def _bind_server(lib):
     lib.syev3_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double]
     lib.syev3_server_release.argtypes = [vp, ctypes.c_uint64]
     lib.syev3_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    lib.syev3_server_inject_failure.argtypes = [vp, ctypes.c_int]
     for f in ("syev3_server_create", "syev3_server_destroy", "syev3_server_submit", "syev3_server_query",
-              "syev3_server_wait", "syev3_server_release", "syev3_server_get_stats"):
+              "syev3_server_wait", "syev3_server_release", "syev3_server_get_stats", "syev3_server_inject_failure"):
         getattr(lib, f).restype = ctypes.c_int
     lib._server_bound = True
 
 
 class Server:
-    """Continuous-batching request server (see include/syev3.h).  Requests
-    are device tensors of packed matrices; results stay in the server's
-    device arena until released."""
+    """Continuous-batching request server with device-resident queues and
+    admission (see include/syev3.h).  Requests are device tensors of packed
+    matrices; results stay in the server's device arena until released."""
 
-    def __init__(self, memory_budget_bytes: int = 16 << 30, num_streams: int = 4, chunk: int = 1 << 18,
-                 max_inflight: int = 2):
+    def __init__(self, memory_budget_bytes: int = 16 << 30, chunk: int = 1 << 18, round_matrices: int = 1 << 21,
+                 max_rounds_in_flight: int = 2):
         self._lib = _load()
         _bind_server(self._lib)
-        cfg = _ServerConfig(memory_budget_bytes, num_streams, chunk, max_inflight)
+        cfg = _ServerConfig(memory_budget_bytes, chunk, round_matrices, max_rounds_in_flight)
         h = ctypes.c_void_p()
         _check(self._lib.syev3_server_create(ctypes.byref(cfg), ctypes.byref(h)), "syev3_server_create")
         self._h = h
@@ -374,6 +380,10 @@ class Server:
     def release(self, ticket: int):
         _check(self._lib.syev3_server_release(self._h, ticket), "syev3_server_release")
         self._keep.pop(ticket, None)
+
+    def inject_failure(self, status: int = SYEV3_ECUDA):
+        """Fail the server as if its next launch returned ``status`` (tests)."""
+        _check(self._lib.syev3_server_inject_failure(self._h, int(status)), "syev3_server_inject_failure")
 
     def stats(self) -> ServerStats:
         st = ServerStats()

@@ -45,7 +45,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version(lib):
-    assert lib.syev3_abi_version() == 1
+    assert lib.syev3_abi_version() == 2
 
 
 def test_host_side_argument_checks(lib):

@@ -253,7 +253,7 @@ def test_inline_refinement_carry(syev3, n, vectors):
     torch.cuda.synchronize()
     assert torch.equal(c1, c2)
     if n >= 129:
-        assert int(c1[2]) > n // 2  # most lanes refined in FP64
+        assert int(c1[2]) > n // 4  # many lanes refined in FP64
     scale = float(lam1.abs().max())
     assert float((lam1 - lam2).abs().max()) <= 4 * parity.EPS32 * scale
     lam_o, U_o = oracle.syev3(A.astype(np.float64))

@@ -54,6 +54,17 @@ def check_against_oracle(A, lam, U, ref):
         parity.compare_f32(A_np, lam.cpu().numpy(), U.cpu().numpy(), lam_o, U_o)
 
 
+def released_stats(srv, timeout_s=10.0):
+    """Server statistics once the device has processed the releases made so
+    far (it frees released results in its next round)."""
+    t0 = time.time()
+    st = srv.stats()
+    while st.arena_used != 0 and time.time() - t0 < timeout_s:
+        time.sleep(0.001)
+        st = srv.stats()
+    return st
+
+
 def standalone(syev3, A, comp):
     lam, U = syev3.syev3_batched(A, compensated=comp)
     torch.cuda.synchronize()
@@ -68,7 +79,7 @@ def test_same_alone_and_in_the_mix(syev3, pools, pool_oracle):
     A64, A32 = pools
     rng = np.random.default_rng(4002)
     budget = 48 << 20
-    srv = syev3.Server(memory_budget_bytes=budget, num_streams=4, chunk=1 << 12, max_inflight=2)
+    srv = syev3.Server(memory_budget_bytes=budget, chunk=1 << 12, round_matrices=1 << 15, max_rounds_in_flight=2)
     reqs = []
     for i in range(160):
         n = int(np.exp(rng.uniform(0, np.log(1 << 17))))
@@ -99,7 +110,7 @@ def test_same_alone_and_in_the_mix(syev3, pools, pool_oracle):
         sl = slice(off, off + A.shape[0])
         check_against_oracle(A, lam, U, (lam_o[sl], U_o[sl]))
         srv.release(tickets[i])
-    st = srv.stats()
+    st = released_stats(srv)
     assert st.completed == len(reqs) and st.waiting == 0 and st.error == 0
     assert st.arena_peak <= budget and st.arena_used == 0
     assert st.chunks > len(reqs)  # large requests were cut into chunks
@@ -113,7 +124,7 @@ def test_small_requests_overtake_a_large_one(syev3, pools):
     # 2^23 matrices in 512 chunks: about 3.4 ms of solving, long against the
     # time the host takes to submit the small requests below.
     A_big = A64.repeat(8, 1)
-    srv = syev3.Server(memory_budget_bytes=2 << 30, num_streams=4, chunk=1 << 14, max_inflight=1)
+    srv = syev3.Server(memory_budget_bytes=2 << 30, chunk=1 << 14, round_matrices=1 << 16, max_rounds_in_flight=1)
     big = srv.submit(A_big)
     while srv.query(big).state == 0:
         time.sleep(0.0001)
@@ -129,13 +140,61 @@ def test_small_requests_overtake_a_large_one(syev3, pools):
 
 def test_budget_is_enforced(syev3, pools):
     A64, _ = pools
-    srv = syev3.Server(memory_budget_bytes=1 << 20, num_streams=2, chunk=1 << 10)
+    srv = syev3.Server(memory_budget_bytes=1 << 20, chunk=1 << 10)
     with pytest.raises(syev3.Syev3Error):
         srv.submit(A64[:20000])  # 20000 x 96 B > 1 MiB: can never be admitted
     ts = [srv.submit(A64[k * 5000:(k + 1) * 5000]) for k in range(12)]  # each ~0.46 MiB: two at a time
     for t in ts:
         assert srv.wait(t, 60.0).state == 2
         srv.release(t)
+    st = released_stats(srv)
+    assert st.arena_peak <= (1 << 20) and st.completed == 12 and st.arena_used == 0
+    srv.close()
+
+
+def test_failure_is_reported_and_frees_nothing(syev3, pools):
+    """A launch failure made on the host (no device fault): requests not yet
+    done fail with the error, waiters wake, later submits are refused, a
+    release frees nothing on the device, and the server still shuts down."""
+    A64, _ = pools
+    srv = syev3.Server(memory_budget_bytes=1 << 30, chunk=1 << 10, round_matrices=1 << 12, max_rounds_in_flight=1)
+    done = srv.submit(A64[:1000])
+    assert srv.wait(done, 60.0).state == 2
+    big = srv.submit(A64[: 1 << 20])  # 1024 rounds of 2^10: still running below
+    while srv.query(big).state == 0:
+        time.sleep(0.0001)
+    srv.inject_failure(syev3.SYEV3_ECUDA)
+    with pytest.raises(syev3.Syev3Error) as e:
+        srv.wait(big, 60.0)
+    assert e.value.status == syev3.SYEV3_ECUDA
+    assert srv.query(big).state == 3
+    used = srv.stats().arena_used
+    assert used > 0
+    srv.release(big)
+    srv.release(done)
+    time.sleep(0.05)
+    assert srv.stats().arena_used == used and srv.stats().error == syev3.SYEV3_ECUDA
+    with pytest.raises(syev3.Syev3Error):
+        srv.submit(A64[:10])
+    srv.close()
+
+
+def test_ring_full_is_refused(syev3, pools):
+    """More outstanding (unreleased) requests than the ring's slots: submit
+    returns SYEV3_EAGAIN, and succeeds again once one is released."""
+    A64, _ = pools
+    srv = syev3.Server(memory_budget_bytes=1 << 30)
+    ts = [srv.submit(A64[i:i + 1]) for i in range(syev3.SERVER_SLOTS)]
+    with pytest.raises(syev3.Syev3Error) as e:
+        srv.submit(A64[:1])
+    assert e.value.status == syev3.SYEV3_EAGAIN
+    for t in ts:
+        assert srv.wait(t, 60.0).state == 2
+    srv.release(ts[0])
+    t = srv.submit(A64[:1])
+    assert srv.wait(t, 60.0).state == 2
+    for x in ts[1:] + [t]:
+        srv.release(x)
     st = srv.stats()
-    assert st.arena_peak <= (1 << 20) and st.completed == 12
+    assert st.completed == syev3.SERVER_SLOTS + 1
     srv.close()
