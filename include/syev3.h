@@ -303,7 +303,7 @@ int syev3_probe_dfma(int64_t iters, double* d_sink, int64_t* dfma_count, syev3_s
 typedef struct syev3_server_s syev3_server;
 
 /* Requests submitted and not yet released, at most. */
-#define SYEV3_SERVER_SLOTS 4096
+#define SYEV3_SERVER_SLOTS 16384
 
 /* Returned by syev3_server_submit when SYEV3_SERVER_SLOTS requests are
  * outstanding (not yet released): release some and submit again. */
@@ -312,7 +312,7 @@ typedef struct syev3_server_s syev3_server;
 typedef struct {
   size_t memory_budget_bytes; /* device arena for results; 0 = 16 GiB */
   int64_t chunk;              /* matrices of one request per round; 0 = 2^18 */
-  int64_t round_matrices;     /* matrices per round over all requests; 0 = 2^21 */
+  int64_t round_matrices;     /* matrices per round over all requests, <= 2^27; 0 = 2^21 */
   int max_rounds_in_flight;   /* rounds queued on the device at once, 1..4; 0 = 2 */
 } syev3_server_config;
 

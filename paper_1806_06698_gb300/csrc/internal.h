@@ -61,7 +61,7 @@ struct ServeItem {
   int64_t tag;         // the owner's reference (the serving runtime's request slot)
 };
 constexpr int kServeTile = 128;       // matrices per tile of both solve kernels
-constexpr int kServeMaxItems = 4096;  // one item per admitted request per round
+constexpr int kServeMaxItems = 16384;  // one item per admitted request per round
 struct ServeList {
   int64_t n_items;
   int64_t n_tiles;

@@ -52,9 +52,10 @@ namespace {
 using namespace syev3;
 
 constexpr int kSlots = SYEV3_SERVER_SLOTS;  // request ring: outstanding requests
+static_assert(kSlots <= kServeMaxItems && kServeMaxItems < (1 << 16), "item counts are 16-bit fields");
 constexpr int kMaxNew = 48;                 // descriptors passed per round
 constexpr int kMaxRel = 96;                 // releases passed per round
-constexpr int kMailRing = 1 << 16;          // mailbox records (>= 2 per slot)
+constexpr int kMailRing = 1 << 17;          // mailbox records: >= 2 per slot per round in flight
 constexpr int64_t kUnit = 256;              // arena granule, bytes
 constexpr int kCtlThreads = 256;
 
@@ -93,6 +94,7 @@ struct DevCtl {
   uint64_t rounds;
   uint64_t items;     // work items issued, all rounds
   int32_t active[kSlots];
+  int64_t take[kSlots];  // the round's matrices per active position (scratch)
   Extent ext[kSlots + 1];
   ServeList lists[3];
 };
@@ -263,6 +265,35 @@ __device__ void arena_free(DevCtl* ctl, int64_t off, int64_t len, int64_t* s_k) 
   __syncthreads();
 }
 
+// Inclusive sum of v over the CTA's kCtlThreads threads (every thread calls
+// it); *total receives the CTA's sum.
+__device__ int64_t cta_inclusive_sum(int64_t v, int64_t* s_warp, int64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kWarps = kCtlThreads / 32;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = lane < kWarps ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kWarps) s_warp[lane] = w;
+  }
+  __syncthreads();
+  const int64_t r = x + (warp > 0 ? s_warp[warp - 1] : 0);
+  *total = s_warp[kWarps - 1];
+  __syncthreads();  // s_warp is reused by the next call
+  return r;
+}
+
 __device__ __forceinline__ uint64_t global_timer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -273,6 +304,8 @@ __global__ void __launch_bounds__(kCtlThreads) k_serve_admit(DevCtl* ctl, DevReq
                                                               const AdmitArgs args) {
   __shared__ int64_t s_k;
   __shared__ int s_stop;
+  __shared__ int64_t s_warp[kCtlThreads / 32];
+  __shared__ int64_t s_first, s_rr;
   const int tid = threadIdx.x;
   // 1. Releases: the host passes only done requests it has not passed before.
   for (int r = 0; r < args.n_rel; ++r) {
@@ -324,55 +357,105 @@ __global__ void __launch_bounds__(kCtlThreads) k_serve_admit(DevCtl* ctl, DevReq
     __syncthreads();
   }
   // 4. This round's work: round-robin over the admitted requests with
-  // matrices left, at most `chunk` each and `round_matrices` in all.
-  if (tid == 0) {
-    for (int l = 0; l < 3; ++l) {
-      ctl->lists[l].n_items = 0;
-      ctl->lists[l].n_tiles = 0;
+  // matrices left, at most `chunk` each and `round_matrices` in all, built
+  // by the whole CTA with prefix sums over the active list taken in
+  // round-robin order (position j is active[(start + j) % na]).
+  const int64_t na = ctl->n_active;
+  const int64_t start = na > 0 ? ctl->rr % na : 0;
+  if (tid == 0) s_first = INT64_MAX;
+  __syncthreads();
+  // 4a. take_j = the part of min(chunk, left) within the round's budget.
+  int64_t carry = 0;
+  for (int64_t j0 = 0; j0 < na; j0 += kCtlThreads) {
+    const int64_t j = j0 + tid;
+    int64_t c = 0;
+    if (j < na) {
+      const DevReq* q = &reqs[ctl->active[(start + j) % na]];
+      c = min(args.chunk, q->n - q->issued);
     }
-    int64_t budget = args.round_matrices, pending = 0, items = 0;
-    const int64_t na = ctl->n_active;
-    const int64_t start = na > 0 ? ctl->rr % na : 0;
-    int64_t stop_at = start;
-    for (int64_t j = 0; j < na; ++j) {
-      const int64_t a = (start + j) % na;
-      DevReq* q = &reqs[ctl->active[a]];
-      const int64_t left = q->n - q->issued;
-      const int64_t c = min(min(args.chunk, left), budget);
-      if (c <= 0) {
-        stop_at = a;
-        break;
-      }
-      ServeList* L = &ctl->lists[q->list];
-      const int64_t es = elem_bytes(q->list);
+    int64_t tot;
+    const int64_t incl = cta_inclusive_sum(c, s_warp, &tot) + carry;
+    if (j < na) {
+      const int64_t t = min(max(args.round_matrices - (incl - c), (int64_t)0), c);
+      ctl->take[j] = t;
+      if (t < c) atomicMin(reinterpret_cast<unsigned long long*>(&s_first), (unsigned long long)j);
+    }
+    carry += tot;
+  }
+  __syncthreads();
+  // 4b. Items: per list, an item index and a first tile from prefix sums of
+  // packed counts (16 bits of items and 21 bits of tiles per list).
+  uint64_t carry_i = 0, carry_t = 0;
+  for (int64_t j0 = 0; j0 < na; j0 += kCtlThreads) {
+    const int64_t j = j0 + tid;
+    int64_t t = 0;
+    int slot = 0, l = 0;
+    if (j < na) {
+      slot = ctl->active[(start + j) % na];
+      t = ctl->take[j];
+      l = reqs[slot].list;
+    }
+    const uint64_t tiles = (uint64_t)((t + kServeTile - 1) / kServeTile);
+    const uint64_t vi = t > 0 ? (1ull << (16 * l)) : 0ull;
+    const uint64_t vt = t > 0 ? (tiles << (21 * l)) : 0ull;
+    int64_t ti, tt;
+    const uint64_t ii = (uint64_t)cta_inclusive_sum((int64_t)vi, s_warp, &ti) + carry_i;
+    const uint64_t it_ = (uint64_t)cta_inclusive_sum((int64_t)vt, s_warp, &tt) + carry_t;
+    if (t > 0) {
+      DevReq* q = &reqs[slot];
+      ServeList* L = &ctl->lists[l];
+      const int64_t idx = (int64_t)(((ii - vi) >> (16 * l)) & 0xffffull);
+      const int64_t es = elem_bytes(l);
       char* out = arena + q->off * kUnit;
-      ServeItem& it = L->items[L->n_items++];
-      it.A = static_cast<const char*>(q->A) + q->issued * 6 * es;
-      it.lam = out + q->issued * 3 * es;
-      it.U = q->vectors ? out + q->lam_units * kUnit + q->issued * 9 * es : nullptr;
-      it.count = c;
-      it.tile_begin = L->n_tiles;
-      it.tag = ctl->active[a];
-      L->n_tiles += (c + kServeTile - 1) / kServeTile;
-      q->issued += c;
-      budget -= c;
-      ++items;
-      stop_at = (a + 1) % na;
+      ServeItem& item = L->items[idx];
+      item.A = static_cast<const char*>(q->A) + q->issued * 6 * es;
+      item.lam = out + q->issued * 3 * es;
+      item.U = q->vectors ? out + q->lam_units * kUnit + q->issued * 9 * es : nullptr;
+      item.count = t;
+      item.tile_begin = (int64_t)(((it_ - vt) >> (21 * l)) & 0x1fffffull);
+      item.tag = slot;
+      q->issued += t;
     }
-    // Drop requests with nothing left to issue, keeping the order, and
-    // start the next round where this one stopped.
-    int64_t w = 0, rr = 0;
-    for (int64_t a = 0; a < na; ++a) {
-      DevReq* q = &reqs[ctl->active[a]];
-      if (a == stop_at) rr = w;
-      if (q->n - q->issued > 0) {
-        pending += q->n - q->issued;
-        ctl->active[w++] = ctl->active[a];
-      }
+    carry_i += (uint64_t)ti;
+    carry_t += (uint64_t)tt;
+  }
+  if (tid == 0) {
+    int64_t items = 0;
+    for (int l = 0; l < 3; ++l) {
+      ctl->lists[l].n_items = (int64_t)((carry_i >> (16 * l)) & 0xffffull);
+      ctl->lists[l].n_tiles = (int64_t)((carry_t >> (21 * l)) & 0x1fffffull);
+      items += ctl->lists[l].n_items;
     }
-    ctl->n_active = w;
-    ctl->rr = w > 0 ? rr % w : 0;
     ctl->items += items;
+  }
+  __syncthreads();
+  // 4c. Drop requests with nothing left to issue, keeping the order; the
+  // next round starts at the first request this one did not serve in full.
+  int64_t w0 = 0, pending = 0;
+  if (tid == 0) s_rr = 0;
+  for (int64_t a0 = 0; a0 < na; a0 += kCtlThreads) {
+    const int64_t a = a0 + tid;
+    int slot = -1;
+    int64_t left = 0;
+    if (a < na) {
+      slot = ctl->active[a];
+      left = reqs[slot].n - reqs[slot].issued;
+    }
+    const int64_t keep = left > 0 ? 1 : 0;
+    int64_t kt, lt;
+    const int64_t pos = cta_inclusive_sum(keep, s_warp, &kt) - keep + w0;
+    cta_inclusive_sum(left, s_warp, &lt);
+    if (keep) {
+      ctl->active[pos] = slot;  // pos <= a: this block was read before the sums' barriers
+      if (s_first != INT64_MAX && a == (start + s_first) % na) s_rr = pos;
+    }
+    w0 += kt;
+    pending += lt;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    ctl->n_active = w0;
+    ctl->rr = w0 > 0 ? s_rr % w0 : 0;
     // Mirror the admission state (the records above first).
     __threadfence_system();
     volatile Mailbox* vm = mb;
@@ -667,7 +750,10 @@ int syev3_server_create(const syev3_server_config* cfg, syev3_server** out) {
   }
   // At most 4 rounds queued: the mailbox ring then holds every record the
   // host has not read yet (2 x kSlots per round).
-  if (c.memory_budget_bytes < (size_t)kUnit || c.chunk < 1 || c.round_matrices < 1 || c.max_rounds_in_flight > 4)
+  // At most 2^27 matrices per round: the round's tiles per list are counted
+  // in 21-bit fields by the admission kernel.
+  if (c.memory_budget_bytes < (size_t)kUnit || c.chunk < 1 || c.round_matrices < 1 ||
+      c.round_matrices > ((int64_t)1 << 27) || c.max_rounds_in_flight > 4)
     return SYEV3_EINVAL;
   auto* s = new syev3_server_s();
   s->cfg = c;

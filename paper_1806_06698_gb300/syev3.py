@@ -312,7 +312,7 @@ class ServerStats(ctypes.Structure):
 
 
 # Requests outstanding (submitted, not released) at most (include/syev3.h).
-SERVER_SLOTS = 4096
+SERVER_SLOTS = 16384
 
 
 def _bind_server(lib):
