@@ -193,6 +193,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+_T0 = time.time()
+
+
+def log(msg: str):
+    """Progress of the legs on stderr (the JSON line stays alone on stdout)."""
+    print(f"[bench {time.time() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+
 def load_peaks():
     try:
         with open(MEASURED_PEAKS) as fh:
@@ -329,9 +337,10 @@ def _fp32_legs(args, dev, stream, barrier, A64_dev):
 
     hbm = load_peaks().get("hbm_gbs", 6686.1)
     out = {}
-    sets = [("mixed_fp32_2^24", inputs.mixed_fp32(args.n)[0]),
-            ("structure_tensors_fp32_2^26", inputs.structure_tensors(4 * args.n).astype(np.float32))]
-    for name, A_np in sets:
+    A_mix, ids_mix = inputs.mixed_fp32(args.n)
+    sets = [("mixed_fp32_2^24", A_mix, ids_mix),
+            ("structure_tensors_fp32_2^26", inputs.structure_tensors(4 * args.n).astype(np.float32), None)]
+    for name, A_np, ids in sets:
         n = A_np.shape[0]
         A = torch.from_numpy(A_np).to(dev)
         lam = torch.empty((n, 3), dtype=torch.float32, device=dev)
@@ -355,11 +364,18 @@ def _fp32_legs(args, dev, stream, barrier, A64_dev):
                 syev3.syev3_batched(A, out=(lam, U), compensated=comp, workspace=work, stream=stream)
 
             total_ms, kms = _timed(step, args.steps, args.warmup, stream, barrier)
+            log(f"  {name} {mode}: {total_ms / args.steps:.3f} ms per step")
             syev3.syev3_batched(A, out=(lam, U), compensated=comp, counters=ctr, workspace=work, stream=stream)
             barrier()
             # Accuracy on the host (no library GEMM in the bench's launch list).
             lam_s, U_s = lam[idx].double().cpu().numpy(), U[idx].double().cpu().numpy()
-            dl = float(np.max(np.max(np.abs(lam_s - lam_ref_h), axis=1) / np.maximum(nrm_h, 1e-300)))
+            dl_each = np.max(np.abs(lam_s - lam_ref_h), axis=1) / np.maximum(nrm_h, 1e-300)
+            dl = float(np.max(dl_each))
+            per_subset = None
+            if ids is not None:
+                sid = ids[idx.cpu().numpy()]
+                per_subset = {inputs.SUBSET_NAMES[k]: float(np.max(dl_each[sid == k]) / 2.0 ** -23)
+                              for k in inputs.SUBSET_NAMES if np.any(sid == k)}
             orth = float(np.max(np.linalg.norm(np.einsum("nki,nkj->nij", U_s, U_s) - np.eye(3), axis=(1, 2))))
             k = statistics.mean(kms)
             gbs = 72 * n / (k * 1e-3) / 1e9
@@ -372,6 +388,7 @@ def _fp32_legs(args, dev, stream, barrier, A64_dev):
                              "peak_source": "MEASURED_PEAKS hbm_gbs"},
                 "fp64_refined_fraction": ctr[2].item() / n if comp else 0.0,
                 "max_dlambda_vs_fp64_kernel_eps32": dl / 2.0 ** -23,
+                "max_dlambda_vs_fp64_kernel_eps32_per_subset": per_subset,
                 "max_orthogonality_eps32": orth / 2.0 ** -23,
                 "accuracy_sample": int(idx.numel()),
             }
@@ -629,6 +646,8 @@ def _serving_leg(args, dev, A64):
     th.start()
     for i in range(m):
         ready.acquire()
+        if i % 20000 == 0:
+            log(f"  serving: request {i} of {m}")
         info = srv.wait(tickets[i], 120.0)
         lat.append((info.t_done_ns - t_arrive[i]) * 1e-6)
         queue.append((info.t_admit_ns - info.t_submit_ns) * 1e-6)
@@ -734,12 +753,19 @@ def run_native(args):
                    load_peaks().get("hbm_gbs", 6686.1), "kernel": "k_syev3_f64<bulk, production, values only>"}
     del lam_only
 
+    log("headline, e2e and eigenvalues-only legs done")
     fp64_peak = measure_fp64_peak(dev, stream)
+    log("FP64 peak probe done")
     fp32 = None if args.fp64_only else _fp32_legs(args, dev, stream, barrier, A)
+    log("precision-form legs done")
     bwd = None if args.fp64_only else _bwd_legs(args, dev, stream, barrier, fp64_peak)
+    log("differentiation-form legs done")
     serving = None if (args.fp64_only or args.serve_seconds <= 0) else _serving_leg(args, dev, A)
+    log("serving leg done")
     study = None if args.fp64_only else _method_study_leg(args, dev, stream, barrier)
+    log("method-study leg done")
     accuracy = None if args.fp64_only else _accuracy_experiment(dev, stream)
+    log("accuracy-experiment leg done")
 
     if rank == 0:
         kms = statistics.mean(kernel_ms)
@@ -785,6 +811,7 @@ def run_native(args):
             line["accuracy_experiment"] = accuracy
         if not args.no_cpu_baseline and ws == 1:  # the host-core baseline: rank 0 at N = 1 only
             line["cpu_baseline"] = cpu_baseline(A_np, n)
+            log("CPU baseline done")
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -212,15 +212,17 @@ __device__ __forceinline__ float bg_step32(const float ab, const float b1, const
   return (f > 0.f && xn < x) ? xn : x;
 }
 
-// mu and nu in FP32 on a fixed schedule: from the start of f64::start32 two
-// Borges-Gragg steps for both problems, straight-line (no lane leaves
-// early, so the warp stays converged).  From these starts two steps reach
-// FP32 accuracy for most problems: the second step moves x by about the
-// error the first one left, and the step converges cubically, so a move
-// below 2^-12 x leaves an error of order 2^-36 x.  more[k] marks a problem
-// whose second step moved x by more than that, or whose small-root start
-// turned out left of the root: the kernel finishes those on a compacted
-// work list with roots32_more.
+// mu and nu in FP32 on a fixed schedule: from the start of f64::start32
+// three Borges-Gragg steps for both problems, straight-line (no lane leaves
+// early, so the warp stays converged; a small-root start found left of the
+// root is replaced by the start of Eq. (7) after the first evaluation).  The
+// last step moves x by about the error the one before left, and the step
+// converges cubically, so a move below 2^-12 x leaves an error of order
+// 2^-36 x.  more[k] marks a problem whose last step moved x by more than
+// that: the kernel finishes those in their own lanes with roots32_more,
+// out of line, so the straight-line code keeps its registers and schedule
+// (a compacted shared-memory work list after two steps, the earlier design,
+// cost 18 % of the kernel in its barriers and code even when empty).
 __device__ __forceinline__ void roots32(const float ab, const float b1[2], const float b2[2], const float g[2],
                                         const float c[2], const float K[2], float x[2], bool more[2]) {
 #pragma unroll
@@ -232,14 +234,18 @@ __device__ __forceinline__ void roots32(const float ab, const float b1[2], const
     const bool restart = model && !(f0 > 0.f);  // the small-root start was not right of the root
     if (restart) x1 = x7;
     const float x2 = bg_step32(ab, b1[k], b2[k], g[k], c[k], K[k], x1, &f1);
-    more[k] = restart || (x1 - x2) > 0x1p-12f * x2;
-    x[k] = x2;
+    float f2;
+    const float x3 = bg_step32(ab, b1[k], b2[k], g[k], c[k], K[k], x2, &f2);
+    more[k] = (x2 - x3) > 0x1p-12f * x3;
+    x[k] = x3;
   }
 }
 
 // Further steps for one problem until f/f' < C eps32 x (Sec. 1.4.1), f <= 0
-// or a stalled step; returns false if kMaxIt32 steps were not enough.
-__device__ bool roots32_more(const float ab, const float b1, const float b2, const float g, float* x) {
+// or a stalled step; returns false if kMaxIt32 steps were not enough.  Not
+// inlined: it runs for few roots, and inlined it would weigh on the
+// registers and scheduling of the kernel's main path.
+__device__ __noinline__ bool roots32_more(const float ab, const float b1, const float b2, const float g, float* x) {
   const float c = b2 * rcp32(ab), K = -g - c;
   for (int it = 0; it < kMaxIt32; ++it) {
     float f, fp;
@@ -316,7 +322,7 @@ __device__ __forceinline__ void finish32_values(const Lane32& L, float mu, float
   l_out[0] = l0; l_out[1] = l1; l_out[2] = l2;
 }
 
-__device__ __forceinline__ void finish32(const Lane32& L, float mu, float nu, float l_out[3], float U[9]) {
+__device__ __forceinline__ void finish32(const Lane32& L, float mu, float nu, float l_out[3], float U[9], int rk[3]) {
   const float a1 = L.a1, a2 = L.a2, b1 = L.b1, b2 = L.b2, g = L.g;
   float l[3], v[3][3];
   if (L.cls == kDiag) {
@@ -379,35 +385,22 @@ __device__ __forceinline__ void finish32(const Lane32& L, float mu, float nu, fl
     x[1][1] = fmaf(L.s, v[1][0], L.c * v[1][1]);
     x[1][2] = v[1][2];
   }
-  float l0 = l[0], l1 = l[1], l2 = l[2];
-  float x00 = x[0][0], x01 = x[0][1], x02 = x[0][2];
-  float x10 = x[1][0], x11 = x[1][1], x12 = x[1][2];
-  float x20 = x[2][0], x21 = x[2][1], x22 = x[2][2];
-  // Ascending and stable: three compare-and-swap steps with strict "<",
-  // written as selects so that no lane branches.
-  auto cswap = [](float& la, float& a0, float& a1_, float& a2_, float& lb, float& b0, float& b1_, float& b2_) {
-    const bool sw = lb < la;
-    const float tl = la, t0 = a0, t1 = a1_, t2 = a2_;
-    la = sw ? lb : la;   lb = sw ? tl : lb;
-    a0 = sw ? b0 : a0;   b0 = sw ? t0 : b0;
-    a1_ = sw ? b1_ : a1_; b1_ = sw ? t1 : b1_;
-    a2_ = sw ? b2_ : a2_; b2_ = sw ? t2 : b2_;
-  };
-  cswap(l0, x00, x01, x02, l1, x10, x11, x12);
-  cswap(l1, x10, x11, x12, l2, x20, x21, x22);
-  cswap(l0, x00, x01, x02, l1, x10, x11, x12);
-  const float ls[3] = {l0, l1, l2};
-  const float xs[3][3] = {{x00, x01, x02}, {x10, x11, x12}, {x20, x21, x22}};
-  // Sign rule: each column's largest-magnitude component (the first of
-  // equals) made positive, by XOR-ing the column's sign bits with that
-  // component's (never zero: at least 1/sqrt(3) in a unit vector).
+  // Stable ascending ranks of the three eigenvalues (strict "<" for the
+  // later index keeps equal values in branch order); the caller stores each
+  // eigenpair at its rank.
+  rk[0] = (int)(l[1] < l[0]) + (int)(l[2] < l[0]);
+  rk[1] = (int)(l[0] <= l[1]) + (int)(l[2] < l[1]);
+  rk[2] = (int)(l[0] <= l[2]) + (int)(l[1] <= l[2]);
+  // Sign rule: each vector's largest-magnitude component (the first of
+  // equals) made positive, by XOR-ing its sign bits with that component's
+  // (never zero: at least 1/sqrt(3) in a unit vector).
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const float y0 = xs[k][0], y1 = xs[k][1], y2 = xs[k][2];
+    const float y0 = x[k][0], y1 = x[k][1], y2 = x[k][2];
     float big = (fabsf(y1) > fabsf(y0)) ? y1 : y0;
     big = (fabsf(y2) > fabsf(big)) ? y2 : big;
     const unsigned sb = __float_as_uint(big) & 0x80000000u;
-    l_out[k] = ls[k];
+    l_out[k] = l[k];
     U[0 * 3 + k] = __uint_as_float(__float_as_uint(y0) ^ sb);
     U[1 * 3 + k] = __uint_as_float(__float_as_uint(y1) ^ sb);
     U[2 * 3 + k] = __uint_as_float(__float_as_uint(y2) ^ sb);
@@ -504,10 +497,6 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
   __shared__ int s_fc[kInl ? kFW : 1];
   __shared__ int64_t s_fg[kInl ? kFW : 1];
   __shared__ int s_nflag;
-  // Roots that need more steps than the fixed schedule: (ab, b1, b2, g, x).
-  __shared__ float s_more[2 * kTPB * 5];
-  __shared__ bool s_more_capped[2 * kTPB];
-  __shared__ int s_nmore;
   __shared__ alignas(8) uint64_t s_bar[2];
   // Serving build: the tile of each buffer; the eigenvector row of each
   // flagged lane in the list (s_fg then holds its eigenvalue row's address).
@@ -524,7 +513,6 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
 
   if (tid == 0) {
     s_nflag = 0;
-    s_nmore = 0;
     if (kBulkIn) {
       mbar_init(&s_bar[0], 1);
       mbar_init(&s_bar[1], 1);
@@ -622,41 +610,16 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
       const float pK[2] = {-pg[0] - pc[0], -pg[1] - pc[1]};
       roots32(ab, pb1, pb2, pg, pc, pK, root, more);
     }
-    // Problems that need more steps: compacted with warp ballots into a
-    // shared work list and finished with every lane of the CTA available.
-    {
-      const unsigned m0 = __ballot_sync(0xffffffffu, more[0]);
-      const unsigned m1 = __ballot_sync(0xffffffffu, more[1]);
-      int slot[2] = {-1, -1};
-      const int total = __popc(m0) + __popc(m1);
-      int wbase = 0;
-      if (lane_id == 0 && total) wbase = atomicAdd(&s_nmore, total);
-      wbase = __shfl_sync(0xffffffffu, wbase, 0);
-      if (more[0]) slot[0] = wbase + __popc(m0 & lt_mask);
-      if (more[1]) slot[1] = wbase + __popc(m0) + __popc(m1 & lt_mask);
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        if (slot[k] >= 0) {
-          float* w = &s_more[slot[k] * 5];
-          w[0] = ab; w[1] = pb1[k]; w[2] = pb2[k]; w[3] = pg[k]; w[4] = root[k];
-        }
-      }
-      __syncthreads();
-      const int nm = s_nmore;
-      for (int i = tid; i < nm; i += kTPB) {
-        float* w = &s_more[i * 5];
-        float x = w[4];
-        s_more_capped[i] = !roots32_more(w[0], w[1], w[2], w[3], &x);
-        w[4] = x;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        if (slot[k] >= 0) {
-          root[k] = s_more[slot[k] * 5 + 4];
-          capped |= s_more_capped[slot[k]];
-        }
-      }
+    // Rare: roots still moving after the straight-line steps, finished in
+    // their own lanes (the warp runs this only when one of its roots needs it).
+    if (__any_sync(0xffffffffu, more[0] || more[1])) {
+      float xa = root[0], xb = root[1];
+      bool ca = false, cb = false;
+      if (more[0]) ca = !roots32_more(ab, pb1[0], pb2[0], pg[0], &xa);
+      if (more[1]) cb = !roots32_more(ab, pb1[1], pb2[1], pg[1], &xb);
+      root[0] = xa;
+      root[1] = xb;
+      capped = capped || ca || cb;
     }
     if (L.cls == kRed) {
       if (kComp) {
@@ -683,6 +646,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
     }
 
     bool flagged = false, nonfinite = false;
+    int rk[3] = {0, 1, 2};  // rank of each eigenpair (ascending); identity for the other paths
     if (L.cls != kIdle) {
       float l[3], U[9];
       if (L.cls == kNonFin) {
@@ -696,19 +660,24 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
         finish32_values(L, root[0], root[1], l);
         unscale3(l, L.e);
       } else {
-        finish32(L, root[0], root[1], l, U);
+        finish32(L, root[0], root[1], l, U, rk);
         if (kComp && L.cls != kDiag) {
-          const float nrm2 = fmaf(l[0], l[0], fmaf(l[1], l[1], l[2] * l[2]));
-          const float gap = fminf(l[1] - l[0], l[2] - l[1]);
+          // the eigenvalues' gaps in ascending order (min, median, max)
+          const float lo = fminf(fminf(l[0], l[1]), l[2]), hi = fmaxf(fmaxf(l[0], l[1]), l[2]);
+          const float md = fmaxf(fminf(l[0], l[1]), fminf(fmaxf(l[0], l[1]), l[2]));
+          const float nrm2 = fmaf(lo, lo, fmaf(md, md, hi * hi));
+          const float gap = fminf(md - lo, hi - md);
           flagged = capped || L.near_defl || (gap * gap < (kClusterTau * kClusterTau) * nrm2);
         }
         unscale3(l, L.e);
       }
 #pragma unroll
-      for (int k = 0; k < 3; ++k) s_lam[tid * 3 + k] = l[k];
+      for (int k = 0; k < 3; ++k) s_lam[tid * 3 + rk[k]] = l[k];
       if (kVectors) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) s_U[tid * 9 + k] = U[k];
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) s_U[tid * 9 + i * 3 + rk[k]] = U[i * 3 + k];
       }
     }
 
@@ -818,10 +787,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
       }
     }
     __syncthreads();
-    if (tid == 0) {
-      s_nflag = 0;
-      s_nmore = 0;
-    }
+    if (tid == 0) s_nflag = 0;
 
     {
       float* dst = kServe ? s_ref[buf].lam : lam_out + base * 3;
