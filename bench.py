@@ -612,11 +612,14 @@ def _serving_leg(args, dev, A64):
     offs = (rng.uniform(0, 1, m) * (A64.shape[0] - sizes + 1)).astype(np.int64)
     srv = syev3.Server(memory_budget_bytes=16 << 30, chunk=SERVE_CHUNK, round_matrices=SERVE_ROUND,
                        max_rounds_in_flight=SERVE_INFLIGHT)
-    for k in range(8):  # warm-up requests
-        srv.wait(srv.submit(A64[: 1 << 16]), 60.0)
+    for k in range(8):  # warm-up requests (released: each holds a slot of the request ring)
+        t = srv.submit(A64[: 1 << 16])
+        srv.wait(t, 60.0)
+        srv.release(t)
     tickets = [None] * m
     t_arrive = np.zeros(m, np.int64)
     retries = [0]
+    failure = [None]
     ready = threading.Semaphore(0)
 
     def client():
@@ -630,22 +633,31 @@ def _serving_leg(args, dev, A64):
                 time.sleep(dt)
             pool = A64 if is64[i] else A32
             t_arrive[i] = time.monotonic_ns()
-            while True:
-                try:
-                    tickets[i] = srv.submit(pool[offs[i]:offs[i] + sizes[i]], compensated=not is64[i])
-                    break
-                except syev3.Syev3Error as e:
-                    if e.status != syev3.SYEV3_EAGAIN:
-                        raise
-                    retries[0] += 1
-                    time.sleep(0.0002)
+            try:
+                while True:
+                    try:
+                        tickets[i] = srv.submit(pool[offs[i]:offs[i] + sizes[i]], compensated=not is64[i])
+                        break
+                    except syev3.Syev3Error as e:
+                        if e.status != syev3.SYEV3_EAGAIN or time.monotonic_ns() - t_arrive[i] > 60e9:
+                            raise
+                        retries[0] += 1
+                        time.sleep(0.0002)
+            except Exception as e:  # hand the failure to the waiting thread instead of hanging it
+                failure[0] = e
+                ready.release()
+                return
             ready.release()
 
     lat, queue, solve, t_first, t_last, waited = [], [], [], None, 0, 0
-    th = threading.Thread(target=client)
+    th = threading.Thread(target=client, daemon=True)
     th.start()
     for i in range(m):
         ready.acquire()
+        if failure[0] is not None:
+            th.join()
+            srv.close()
+            raise RuntimeError(f"serving client failed at request {i}: {failure[0]}")
         if i % 20000 == 0:
             log(f"  serving: request {i} of {m}")
         info = srv.wait(tickets[i], 120.0)
