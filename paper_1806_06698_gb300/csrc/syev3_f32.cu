@@ -32,6 +32,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -848,11 +849,16 @@ int blocks_per_sm_f32() {
   return cached;
 }
 
+// per_sm_cap > 0: at most that many CTAs per SM (room left for a kernel
+// that runs beside this one).
 template <bool kBulkIn, int kMode, bool kVectors = true>
 cudaError_t launch(const float* A, int64_t n, float* lam, float* U, unsigned long long* counters,
-                   FlagRec* flag_list, unsigned long long* flag_count, cudaStream_t stream, int sms) {
+                   FlagRec* flag_list, unsigned long long* flag_count, cudaStream_t stream, int sms,
+                   int per_sm_cap = 0) {
   const int64_t n_tiles = (n + kTPB - 1) / kTPB;
-  const int64_t resident = (int64_t)sms * blocks_per_sm_f32<kBulkIn, kMode, kVectors>();
+  int per_sm = blocks_per_sm_f32<kBulkIn, kMode, kVectors>();
+  if (per_sm_cap > 0 && per_sm > per_sm_cap) per_sm = per_sm_cap;
+  const int64_t resident = (int64_t)sms * per_sm;
   const int grid = (int)(n_tiles < resident ? n_tiles : resident);
   k_syev3_f32<kBulkIn, kMode, kVectors>
       <<<grid, kTPB, 0, stream>>>(A, n, lam, U, counters, flag_list, flag_count, nullptr);
@@ -939,6 +945,59 @@ cudaError_t launch_f32_serve(const ServeList* list, bool compensated, unsigned l
 
 size_t f32c_workspace_bytes(int64_t n) { return kFlagListOffset + (size_t)n * sizeof(FlagRec); }
 
+namespace {
+
+// Pipelined deferred path: a batch of at least kPipeMin matrices is cut into
+// kPipeChunks runs of whole tiles; the FP32 kernel solves the runs one after
+// the other on the caller's stream, and the refinement of run c starts on a
+// side stream (after an event recorded behind run c's FP32 kernel) while the
+// FP32 kernel works on run c + 1.  The FP32 grid leaves room for
+// kPipeRefinePerSM refinement CTAs on every SM, so the refinement -- bound by
+// the FP64 pipe -- runs beside the FP32 solve, which is bound by instruction
+// issue.  The caller's stream waits for the side stream at the end.  The
+// side stream and the events are created once per device, and one call's
+// records and waits are enqueued under a lock so that calls from several
+// host threads do not interleave them.
+constexpr int64_t kPipeMin = (int64_t)1 << 21;
+constexpr int kPipeChunks = 8;        // counters: 2 per run, 16 B x 8 <= kFlagListOffset
+// Refinement CTAs per SM beside the FP32 kernel (measured on the 2^24 mixed
+// batch: 1, 2, 3, 4, 5, 6 gave 1.39, 1.33, 1.59, 1.53, 1.54, 1.48e10
+// eigensolves/s; 16 runs instead of 8 were slower, 4 the same; without the
+// pipeline 1.37e10).  With 3, the register file holds 9 FP32 CTAs and 2
+// refinement CTAs per SM.
+constexpr int kPipeRefinePerSM = 3;
+static_assert(2 * sizeof(unsigned long long) * kPipeChunks <= kFlagListOffset, "run counters fit");
+constexpr int kPipeMaxDevices = 64;
+
+struct Pipe {
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev[kPipeChunks + 1] = {};
+};
+std::mutex g_pipe_mu;
+Pipe g_pipe[kPipeMaxDevices];
+
+cudaError_t pipe_for(int dev, Pipe** out) {
+  Pipe& P = g_pipe[dev];
+  if (P.side == nullptr) {
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i <= kPipeChunks; ++i) {
+      e = cudaEventCreateWithFlags(&P.ev[i], cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        for (int j = 0; j < i; ++j) cudaEventDestroy(P.ev[j]);
+        cudaStreamDestroy(s);
+        return e;
+      }
+    }
+    P.side = s;
+  }
+  *out = &P;
+  return cudaSuccess;
+}
+
+}  // namespace
+
 cudaError_t launch_f32c_deferred(const float* A, int64_t n, float* lam, float* U, unsigned long long* counters,
                                  void* work, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
@@ -949,14 +1008,48 @@ cudaError_t launch_f32c_deferred(const float* A, int64_t n, float* lam, float* U
   if (e != cudaSuccess) return e;
   auto* count = static_cast<unsigned long long*>(work);
   auto* list = reinterpret_cast<FlagRec*>(static_cast<char*>(work) + kFlagListOffset);
-  e = cudaMemsetAsync(count, 0, 2 * sizeof(unsigned long long), stream);
+  const bool bulk = (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+  if (n < kPipeMin || dev < 0 || dev >= kPipeMaxDevices) {
+    e = cudaMemsetAsync(count, 0, 2 * sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return e;
+    e = bulk ? launch<true, kDeferred>(A, n, lam, U, counters, list, count, stream, sms)
+             : launch<false, kDeferred>(A, n, lam, U, counters, list, count, stream, sms);
+    if (e != cudaSuccess) return e;
+    k_refine_f32<<<sms * refine_blocks_per_sm(), kRefineTPB, 0, stream>>>(list, count, n, A, lam, U, counters);
+    return cudaGetLastError();
+  }
+  std::lock_guard<std::mutex> hold(g_pipe_mu);
+  Pipe* P = nullptr;
+  e = pipe_for(dev, &P);
   if (e != cudaSuccess) return e;
-  e = ((reinterpret_cast<uintptr_t>(A) & 15) == 0)
-          ? launch<true, kDeferred>(A, n, lam, U, counters, list, count, stream, sms)
-          : launch<false, kDeferred>(A, n, lam, U, counters, list, count, stream, sms);
+  // Runs of whole tiles (128 matrices: every run starts 16-byte aligned in
+  // all three arrays when the batch does); run c uses counters [2c, 2c+1]
+  // and the list records [start, start + len) of its own matrices.
+  const int64_t len = ((n + kPipeChunks - 1) / kPipeChunks + kTPB - 1) / kTPB * kTPB;
+  e = cudaMemsetAsync(count, 0, 2 * sizeof(unsigned long long) * kPipeChunks, stream);
   if (e != cudaSuccess) return e;
-  k_refine_f32<<<sms * refine_blocks_per_sm(), kRefineTPB, 0, stream>>>(list, count, n, A, lam, U, counters);
-  return cudaGetLastError();
+  const int cap = blocks_per_sm_f32<true, kDeferred, true>() - kPipeRefinePerSM;
+  for (int c = 0; c < kPipeChunks; ++c) {
+    const int64_t start = c * len;
+    if (start >= n) break;
+    const int64_t m = (n - start) < len ? (n - start) : len;
+    const float* Ac = A + start * 6;
+    float* lc = lam + start * 3;
+    float* Uc = U ? U + start * 9 : nullptr;
+    unsigned long long* cc = count + 2 * c;
+    e = bulk ? launch<true, kDeferred>(Ac, m, lc, Uc, counters, list + start, cc, stream, sms, cap > 0 ? cap : 1)
+             : launch<false, kDeferred>(Ac, m, lc, Uc, counters, list + start, cc, stream, sms, cap > 0 ? cap : 1);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(P->ev[c], stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->side, P->ev[c], 0);
+    if (e != cudaSuccess) return e;
+    k_refine_f32<<<sms * kPipeRefinePerSM, kRefineTPB, 0, P->side>>>(list + start, cc, m, Ac, lc, Uc, counters);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaEventRecord(P->ev[kPipeChunks], P->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, P->ev[kPipeChunks], 0);
+  return e;
 }
 
 cudaError_t take_flags_f32(unsigned* flags) {

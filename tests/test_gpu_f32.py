@@ -296,3 +296,38 @@ def test_batch_beyond_32_bit_element_indices(syev3):
     vec_gap_filtered_compare(As, lam[idx].cpu().numpy(), U[idx].cpu().numpy(), lam_o, U_o)
     del A, lam, U
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("offset", [0, 1])
+def test_workspace_pipeline_ragged(syev3, offset):
+    """From 2^21 matrices on, syev3_batched_ws pipelines the FP32 solve and
+    the FP64 refinement over 8 runs on two streams.  A ragged batch (the
+    last run partial) with the input 16-byte aligned or not: the same
+    counters as the single-kernel compensated path, eigenvalues within
+    4 eps32 of it, and the FP32 bar against the oracle on every matrix."""
+    n = (1 << 21) + 3 * 128 + 77
+    A, _ = inputs.mixed_fp32(n + offset, seed=2120)
+    buf = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    At = buf[offset:]  # offset 1: 24 bytes from the allocation, not 16-byte aligned
+    A = A[offset:]
+    c1 = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device="cuda")
+    lam1, U1 = syev3.syev3_batched(At, compensated=True, counters=c1)
+    nb = syev3.workspace_bytes(n, At.dtype, compensated=True)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        c2 = torch.zeros(syev3.NUM_COUNTERS, dtype=torch.int64, device="cuda")
+        lam2, U2 = syev3.syev3_batched(At, compensated=True, counters=c2, workspace=ws)
+        torch.cuda.synchronize()
+        assert torch.equal(c1, c2), (c1, c2)
+        assert int(c2[2]) > 0
+        nrm = torch.from_numpy(parity.fro(A.astype(np.float64))).cuda()
+        dl = ((lam2.double() - lam1.double()).abs().amax(dim=1) / nrm.clamp_min(1e-300)).max().item()
+        assert dl <= 4 * parity.EPS32, dl
+    lam_o, U_o = parity.oracle_all_cores(A.astype(np.float64))
+    lam_h, U_h = lam2.cpu().numpy(), U2.cpu().numpy()
+
+    def check(lo, hi):
+        sl = slice(lo, hi)
+        parity.compare_f32(A[sl], lam_h[sl], U_h[sl], lam_o[sl], U_o[sl])
+
+    parity.chunked(check, n)
