@@ -883,16 +883,15 @@ def record_traffic(args):
         rows = list(csv.reader(line for line in fh if line.startswith('"')))
     hdr = rows[0]
     ki, mi, ui, vi, ii = (hdr.index(k) for k in ("Kernel Name", "Metric Name", "Metric Unit", "Metric Value", "ID"))
-    launch, got = None, {}
+    # Every launch of the case's kernel in the capture, summed: the
+    # pipelined compensated path launches the FP32 kernel once per run.
+    launches, got = set(), {"dram__bytes_read.sum": 0.0, "dram__bytes_write.sum": 0.0}
     for r in rows[1:]:
         if kernel not in r[ki]:
             continue
-        if launch is None:
-            launch = r[ii]
-        if r[ii] != launch:
-            break
-        if r[mi].startswith("dram__bytes_"):
-            got[r[mi]] = float(r[vi].replace(",", "")) * _BYTE_UNITS[r[ui]]
+        launches.add(r[ii])
+        if r[mi] in got:
+            got[r[mi]] += float(r[vi].replace(",", "")) * _BYTE_UNITS[r[ui]]
     rd, wr = got["dram__bytes_read.sum"], got["dram__bytes_write.sum"]
     try:
         with open(TRAFFIC_JSON) as fh:
@@ -900,9 +899,10 @@ def record_traffic(args):
     except (OSError, ValueError):
         table = {}
     table[case] = {"kernel": kernel, "workload": TRAFFIC_CASES[case][2], "n": n, "sources": sources_hash(case),
+                   "launches": len(launches),
                    "dram_read_bytes": rd, "dram_write_bytes": wr, "bytes_per_matrix": (rd + wr) / n,
                    "command": f"ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-                              f"--clock-control none -k regex:{kernel} -c 1 --csv "
+                              f"--clock-control none -k regex:{kernel} -c {len(launches)} --csv "
                               f"python bench.py --profile-case {case} --n {n}"}
     with open(TRAFFIC_JSON, "w") as fh:
         json.dump(table, fh, indent=1, sort_keys=True)

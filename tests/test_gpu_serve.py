@@ -198,3 +198,39 @@ def test_ring_full_is_refused(syev3, pools):
     st = srv.stats()
     assert st.completed == syev3.SERVER_SLOTS + 1
     srv.close()
+
+
+def test_eigenvalues_only_requests(syev3, pools, pool_oracle):
+    """Requests without eigenvectors (the arena holds only their eigenvalues;
+    the serving solve kernels skip the vector stores of those tiles), mixed
+    with requests that want them: eigenvalues equal to a standalone
+    eigenvalues-only call bit for bit and within the oracle's bars."""
+    A64, A32 = pools
+    rng = np.random.default_rng(4010)
+    srv = syev3.Server(memory_budget_bytes=256 << 20, chunk=1 << 13, round_matrices=1 << 16)
+    reqs = []
+    for i in range(40):
+        n = int(np.exp(rng.uniform(0, np.log(1 << 16))))
+        is64 = bool(rng.uniform() < 0.6)
+        pool = A64 if is64 else A32
+        off = int(rng.integers(0, pool.shape[0] - n))
+        vectors = bool(i % 2)
+        comp = (not is64) and bool(rng.uniform() < 0.5)
+        t = srv.submit(pool[off:off + n], compensated=comp, vectors=vectors)
+        reqs.append((t, pool[off:off + n], comp, is64, off, vectors))
+    for t, A, comp, is64, off, vectors in reqs:
+        info = srv.wait(t, 60.0)
+        assert info.state == 2
+        lam, U = srv.results(t)
+        assert (U is None) == (not vectors)
+        lam_s, _ = syev3.syev3_batched(A, compensated=comp, vectors=False)
+        torch.cuda.synchronize()
+        assert torch.equal(lam, lam_s)
+        lam_o, _ = pool_oracle[0 if is64 else 1]
+        sl = slice(off, off + A.shape[0])
+        eps, tol = (parity.EPS64, 8) if is64 else (parity.EPS32, 64)
+        parity.compare(A.cpu().numpy().astype(np.float64), lam.cpu().numpy(), None, lam_o[sl], None, eps=eps,
+                       lam_tol=tol, res_tol=0, orth_tol=0, vec_tol=0)
+        srv.release(t)
+    assert released_stats(srv).arena_used == 0
+    srv.close()
