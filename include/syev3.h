@@ -103,7 +103,13 @@ int syev3_batched_ex(const void* A_packed6, int64_t n, void* lambda, void* U, in
  * no FP64 code (fewer registers, more resident warps): the faster path when
  * few lanes are flagged (syev3_batched refines them in the FP32 kernel, in
  * whole warps gathered across tiles, and is the faster one when many are).
- * Results equal those of syev3_batched up to rounding.
+ * Results equal those of syev3_batched up to rounding.  From 2^21 matrices
+ * on, the FP32 solve runs in 8 runs on `stream` and each run's refinement
+ * on a side stream beside the next run's solve (events order them; `stream`
+ * waits for the side stream before anything queued after the call); the
+ * side stream and its events are created by the library on the first such
+ * call for a device and kept, and calls from several host threads enqueue
+ * their work one after the other.
  * Other dtypes ignore the workspace (it may be NULL).
  *   d_workspace     : device, at least syev3_workspace_bytes(n, dtype) bytes,
  *                     256-byte aligned, caller-owned; must not overlap the

@@ -23,7 +23,8 @@
 // ballots into a shared-memory list and refined in whole warps, the rest
 // carried from tile to tile, so the FP64 work runs on as few warps as
 // possible; no global scratch memory is used (syev3_batched_ws instead
-// appends them to a list in a workspace for k_refine_f32).
+// appends them to a list in a workspace for k_refine_f32, which runs beside
+// the FP32 solve on a second stream for large batches).
 //
 // Memory path as in the FP64 kernel: tiles of kTPB records (24 B each) by
 // 1-D bulk copy into shared memory, double-buffered on mbarriers; results
