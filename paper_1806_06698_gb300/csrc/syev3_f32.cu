@@ -61,6 +61,10 @@ constexpr float kTinySpike32 = 0x1p-60f;  // spikes below this are zeroed (beta-
 constexpr float kNearDefl = 2.0f;         // near-deflated: test sides within this factor
 constexpr float kClusterTau = 0x1p-23f;   // clustered: relative gap below this
 constexpr double kResidualTol = 16.0 * 0x1p-23;  // FP64 residual check, times ||A||_F
+// Plain form: a last zero-finder move above kMoveTol x (relative error of
+// order kMoveTol^3 = 2^-24 after the cubically convergent step) sends the
+// root to further steps.
+constexpr float kMoveTol = 0x1p-8f;
 constexpr int kPlain = 0, kInline = 1, kDeferred = 2;  // modes of k_syev3_f32
 
 constexpr int kDiag = f64::kDiagonal, kDefl = f64::kDeflated, kRed = f64::kReduced,
@@ -183,6 +187,18 @@ __device__ __forceinline__ Lane32 make_lane32(const float a_in[6]) {
   return L;
 }
 
+// The zero of phi_j (the model of Eq. (5) through x) taken directly: the
+// root of omega_0 y^2 - sigma y - omega_1 = 0, for a step Delta >= x/2 (a
+// start far right of the root).  r1 = 1/x, r2 = 1/(x + ab).
+__device__ __forceinline__ float phi_zero32(const float b1, const float b2, const float x, const float r1,
+                                            const float r2, const float w0, const float f) {
+  const float xr = x * r2;
+  const float w1 = fmaf(b2 * xr, xr * xr, b1);
+  const float sg = fmaf(w0, x, -fmaf(w1, r1, f));
+  const float rt = sqrt32(fmaf(sg, sg, 4.f * w0 * w1));
+  return (sg > 0.f) ? (sg + rt) * rcp32(2.f * w0) : (2.f * w1) * rcp32(rt - sg);
+}
+
 // One Borges-Gragg step in FP32 (Sec. 1.4.1) from x: returns x_{j+1}, or x
 // itself when f(x) <= 0 (at or past the root: rounding level).  For x < ab,
 // f = x + K - b1/x + c x/(x+ab) (the cancellation-free form); x_{j+1} is
@@ -204,27 +220,93 @@ __device__ __forceinline__ float bg_step32(const float ab, const float b1, const
   const float z = (-4.f * w0) * (r1 * rb) * fr;
   const float delta = 2.f * fr * rcp32(1.f + sqrt32(fmaxf(0.f, 1.f + z)));
   float xn = x - delta;
-  if (!(delta < 0.5f * x)) {  // rare: the zero of phi_j directly
-    const float xr = x * r2;
-    const float w1 = fmaf(b2 * xr, xr * xr, b1);
-    const float sg = fmaf(w0, x, -fmaf(w1, r1, f));
-    const float rt = sqrt32(fmaf(sg, sg, 4.f * w0 * w1));
-    xn = (sg > 0.f) ? (sg + rt) * rcp32(2.f * w0) : (2.f * w1) * rcp32(rt - sg);
-  }
+  if (!(delta < 0.5f * x)) xn = phi_zero32(b1, b2, x, r1, r2, w0, f);  // rare
   return (f > 0.f && xn < x) ? xn : x;
 }
 
-// mu and nu in FP32 on a fixed schedule: from the start of f64::start32
-// three Borges-Gragg steps for both problems, straight-line (no lane leaves
-// early, so the warp stays converged; a small-root start found left of the
-// root is replaced by the start of Eq. (7) after the first evaluation).  The
-// last step moves x by about the error the one before left, and the step
-// converges cubically, so a move below 2^-12 x leaves an error of order
-// 2^-36 x.  more[k] marks a problem whose last step moved x by more than
-// that: the kernel finishes those in their own lanes with roots32_more,
-// out of line, so the straight-line code keeps its registers and schedule
-// (a compacted shared-memory work list after two steps, the earlier design,
-// cost 18 % of the kernel in its barriers and code even when empty).
+// Pairs of FP32 values -- .x for the problem of mu, .y for that of nu -- on
+// the packed FP32 instructions of sm_100 and later, which perform the same
+// correctly rounded operation on both halves: the two problems of a lane run
+// the same expressions, so they issue as one instruction stream.  A
+// difference a - b is formed as fma(b, -1, a), which rounds the exact
+// difference once, as a subtraction does.  Reciprocals, roots, comparisons
+// and selections stay per half.
+using P2 = float2;
+__device__ __forceinline__ P2 pp(const float a) { return make_float2(a, a); }
+__device__ __forceinline__ P2 padd(const P2 a, const P2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ P2 psub(const P2 a, const P2 b) { return __ffma2_rn(b, pp(-1.f), a); }
+__device__ __forceinline__ P2 pmul(const P2 a, const P2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ P2 pfma(const P2 a, const P2 b, const P2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ P2 prcp(const P2 a) { return make_float2(rcp32(a.x), rcp32(a.y)); }
+__device__ __forceinline__ P2 psqrt(const P2 a) { return make_float2(sqrt32(a.x), sqrt32(a.y)); }
+__device__ __forceinline__ P2 psel(const bool px, const bool py, const P2 a, const P2 b) {
+  return make_float2(px ? a.x : b.x, py ? a.y : b.y);
+}
+
+// The starts of f64::start32 for both problems: the zero x7 of the limit
+// model of Eq. (7), and the small-root model's start taken where it applies
+// (model[k]).  rab = 1/ab.
+__device__ __forceinline__ P2 start32x2(const P2 ab, const P2 rab, const P2 b1, const P2 b2, const P2 g, const P2 c,
+                                       const P2 K, P2& x7, bool model[2]) {
+  const P2 hg = pmul(pp(0.5f), g), bs = padd(b1, b2);
+  const P2 rt = psqrt(pfma(hg, hg, bs));
+  x7 = psel(g.x >= 0.f, g.y >= 0.f, padd(hg, rt), pmul(bs, prcp(psub(rt, hg))));
+  const P2 c2 = pfma(c, rab, pp(1.f));
+  const P2 disc = psqrt(pfma(K, K, pmul(pmul(pp(4.f), c2), b1)));
+  const bool kx = K.x >= 0.f, ky = K.y >= 0.f;
+  const P2 xm = pmul(psel(kx, ky, padd(b1, b1), psub(disc, K)), prcp(psel(kx, ky, padd(K, disc), padd(c2, c2))));
+  const P2 r1 = prcp(xm), r2 = prcp(padd(xm, ab));
+  const P2 fpm = pfma(pmul(b2, r2), r2, pfma(pmul(b1, r1), r1, pp(1.f)));
+  const P2 x0 = padd(xm, pfma(pmul(pmul(padd(c, c), xm), xm), prcp(pmul(pmul(ab, ab), fpm)),
+                             pmul(pp(0x1p-20f), xm)));
+  model[0] = (xm.x > 0.f) && (xm.x < 0.0625f * ab.x) && (x0.x < x7.x);
+  model[1] = (xm.y > 0.f) && (xm.y < 0.0625f * ab.y) && (x0.y < x7.y);
+  return psel(model[0], model[1], x0, x7);
+}
+
+// The step of bg_step32 for both problems (nb2 = -b2, ng = -g); *fx
+// receives f(x).
+template <bool kBranchFree>
+__device__ __forceinline__ P2 bg_step32x2(const P2 ab, const P2 b1, const P2 b2, const P2 nb2, const P2 ng,
+                                         const P2 c, const P2 K, const P2 x, P2* fx) {
+  const P2 r1 = prcp(x), r2 = prcp(padd(x, ab));
+  const P2 t1 = pmul(b1, r1);
+  const bool sx = x.x < ab.x, sy = x.y < ab.y;
+  // x + K - b1/x + c x/(x+ab) below ab, x - g - b1/x - b2/(x+ab) above
+  const P2 f = padd(psub(padd(x, psel(sx, sy, K, ng)), t1), pmul(psel(sx, sy, pmul(c, x), nb2), r2));
+  *fx = f;
+  const P2 t2 = pmul(b2, r2);
+  const P2 fp = pfma(t2, r2, pfma(t1, r1, pp(1.f)));
+  const P2 w0 = pfma(pmul(t2, ab), pmul(r2, r2), pp(1.f));
+  const P2 rb = prcp(pfma(f, r1, fp));
+  const P2 fr = pmul(f, rb);
+  const P2 q = padd(pp(1.f), pmul(pmul(pmul(pp(-4.f), w0), pmul(r1, rb)), fr));
+  const P2 delta = pmul(padd(fr, fr), prcp(padd(pp(1.f), psqrt(make_float2(fmaxf(0.f, q.x), fmaxf(0.f, q.y))))));
+  P2 xn = psub(x, delta);
+  const P2 d2 = padd(delta, delta);  // Delta >= x/2 (exact doubling)
+  const bool dx = !(d2.x < x.x), dy = !(d2.y < x.y);
+  if constexpr (kBranchFree) {
+    // the zero of phi_j for both problems, kept where Delta >= x/2
+    const P2 xr = pmul(x, r2);
+    const P2 w1 = pfma(pmul(b2, xr), pmul(xr, xr), b1);
+    const P2 sg = pfma(w0, x, pmul(pfma(w1, r1, f), pp(-1.f)));
+    const P2 rt = psqrt(pfma(sg, sg, pmul(pmul(pp(4.f), w0), w1)));
+    const bool px = sg.x > 0.f, py = sg.y > 0.f;
+    const P2 xd = pmul(psel(px, py, padd(sg, rt), padd(w1, w1)), prcp(psel(px, py, padd(w0, w0), psub(rt, sg))));
+    xn = psel(dx, dy, xd, xn);
+  } else {
+    if (dx || dy) {  // rare
+      if (dx) xn.x = phi_zero32(b1.x, b2.x, x.x, r1.x, r2.x, w0.x, f.x);
+      if (dy) xn.y = phi_zero32(b1.y, b2.y, x.y, r1.y, r2.y, w0.y, f.y);
+    }
+  }
+  return psel(f.x > 0.f && xn.x < x.x, f.y > 0.f && xn.y < x.y, xn, x);
+}
+
+// The schedule of roots32x2 (below) one problem at a time, for the
+// compensated forms: their builds keep 40 registers, room for the FP64
+// refinement CTAs that run beside them.  more[k] as in roots32x2, for a move
+// above 2^-12 x; these forms finish such roots in the warp, right after.
 __device__ __forceinline__ void roots32(const float ab, const float b1[2], const float b2[2], const float g[2],
                                         const float c[2], const float K[2], float x[2], bool more[2]) {
 #pragma unroll
@@ -243,6 +325,33 @@ __device__ __forceinline__ void roots32(const float ab, const float b1[2], const
   }
 }
 
+// mu and nu in FP32 on a fixed schedule, both problems paired: from the
+// starts of start32x2 three Borges-Gragg steps, straight-line (no lane
+// leaves early, so the warp stays converged; a small-root start found left
+// of the root is replaced by the start of Eq. (7) after the first
+// evaluation).  The last step moves x by about the error the one before
+// left, and the step converges cubically, so a move below kMoveTol x leaves
+// an error of order kMoveTol^3 x.  more[k] marks a problem whose last step
+// moved x by more than that; the kernel finishes those roots apart from the
+// straight-line code (see k_syev3_f32).
+__device__ __forceinline__ void roots32x2(const P2 ab, const P2 rab, const P2 b1, const P2 b2, const P2 g,
+                                          const P2 c, const P2 K, float x[2], bool more[2]) {
+  const P2 nb2 = make_float2(-b2.x, -b2.y), ng = make_float2(-g.x, -g.y);
+  P2 x7, f0, f1, f2;
+  bool model[2];
+  const P2 x0 = start32x2(ab, rab, b1, b2, g, c, K, x7, model);
+  P2 x1 = bg_step32x2<true>(ab, b1, b2, nb2, ng, c, K, x0, &f0);
+  // the small-root start was not right of the root: restart from Eq. (7)'s
+  x1 = psel(model[0] && !(f0.x > 0.f), model[1] && !(f0.y > 0.f), x7, x1);
+  const P2 x2 = bg_step32x2<false>(ab, b1, b2, nb2, ng, c, K, x1, &f1);
+  const P2 x3 = bg_step32x2<false>(ab, b1, b2, nb2, ng, c, K, x2, &f2);
+  const P2 mv = psub(x2, x3), th = pmul(pp(kMoveTol), x3);
+  more[0] = mv.x > th.x;
+  more[1] = mv.y > th.y;
+  x[0] = x3.x;
+  x[1] = x3.y;
+}
+
 // Further steps for one problem until f/f' < C eps32 x (Sec. 1.4.1), f <= 0
 // or a stalled step; returns false if kMaxIt32 steps were not enough.  Not
 // inlined: it runs for few roots, and inlined it would weigh on the
@@ -257,6 +366,18 @@ __device__ __noinline__ bool roots32_more(const float ab, const float b1, const 
     if (!go) return true;
   }
   return false;
+}
+
+// The two problems' data of a reduced arrow (Sec. 1.2): problem 0 (mu)
+// has spikes (b1^2, b2^2) and gap g - a1, problem 1 (nu) the spikes swapped
+// and a2 - g; ab = a1 - a2.
+__device__ __forceinline__ void roots_setup32(const Lane32& L, const float ab, float b1[2], float b2[2],
+                                              float g[2]) {
+  (void)ab;
+  const P2 bb = pmul(make_float2(L.b1, L.b2), make_float2(L.b1, L.b2));
+  const P2 gg = psub(make_float2(L.g, L.a2), make_float2(L.a1, L.g));
+  b1[0] = bb.x; b1[1] = bb.y; b2[0] = bb.y; b2[1] = bb.x;
+  g[0] = gg.x; g[1] = gg.y;
 }
 
 // Double-float value of the spectral function at x (FP32 data exact), and
@@ -296,11 +417,61 @@ __device__ __forceinline__ float newton_ff(const F2 ab, const F2 b1, const F2 b2
   return (xn > 0.f) ? xn : x;
 }
 
+// newton_ff for both problems at once (pairs as in roots32x2): each
+// double-float datum as a (head pair, low pair); ng = -g.  The same
+// expressions as newton_ff, term by term.
+__device__ __forceinline__ P2 pneg(const P2 a) { return pmul(a, pp(-1.f)); }
+
+__device__ __forceinline__ void ptwo_sum(const P2 a, const P2 b, P2& s, P2& e) {
+  s = padd(a, b);
+  const P2 bb = psub(s, a);
+  e = padd(psub(a, psub(s, bb)), psub(b, bb));
+}
+
+__device__ __forceinline__ P2 newton_ff2(const P2 abh, const P2 abl, const P2 b1h, const P2 b1l, const P2 b2h,
+                                        const P2 b2l, const P2 ngh, const P2 ngl, const P2 ch, const P2 cl,
+                                        const P2 Kh, const P2 Kl, const P2 x) {
+  const P2 r1 = prcp(x), nx = pneg(x);
+  P2 sh, s0l;
+  ptwo_sum(x, abh, sh, s0l);
+  const P2 sl = padd(s0l, abl);  // x + ab = sh + sl
+  const P2 r2 = prcp(sh);
+  // b1 / x: the quotient's head and the remainder over x.
+  const P2 q1 = pmul(b1h, r1);
+  const P2 q1l = pmul(padd(pfma(q1, nx, b1h), b1l), r1);
+  // Last term: + c x / (x + ab) below ab (the cancellation-free form),
+  // - b2 / (x + ab) above; numerator (nh, nl), quotient (q2, q2l).
+  const bool sx = x.x < abh.x, sy = x.y < abh.y;
+  const P2 cx = pmul(ch, x);
+  const P2 nh = psel(sx, sy, cx, b2h);
+  const P2 nl = psel(sx, sy, pfma(cl, x, pfma(ch, x, pneg(cx))), b2l);
+  const P2 q2 = pmul(nh, r2), nq2 = pneg(q2);
+  const P2 q2l = pmul(pfma(nq2, sl, padd(pfma(nq2, sh, nh), nl)), r2);
+  const P2 sg = psel(sx, sy, pp(1.f), pp(-1.f));
+  const P2 th = pmul(q2, sg), tl = pmul(q2l, sg);
+  const P2 lh = psel(sx, sy, Kh, ngh), ll = psel(sx, sy, Kl, ngl);
+  // Sum2 over x + lead - b1/x + last.
+  P2 uh, ul, vh, vl, wh, wl;
+  ptwo_sum(x, lh, uh, ul);
+  vh = psub(uh, q1);  // TwoSum(u.h, -q1)
+  {
+    const P2 bb = psub(vh, uh);
+    vl = psub(psub(uh, psub(vh, bb)), padd(q1, bb));
+  }
+  ptwo_sum(vh, th, wh, wl);
+  const P2 f = padd(wh, padd(padd(padd(ul, vl), padd(wl, ll)), psub(tl, q1l)));
+  const P2 fp = pfma(pmul(b2h, r2), r2, pfma(q1, r1, pp(1.f)));
+  const P2 xn = pfma(pneg(f), prcp(fp), x);
+  return psel(xn.x > 0.f, xn.y > 0.f, xn, x);
+}
+
 // Eigenpairs of a classified lane in FP32 (scaled frame); returns eigenvalues
 // ascending in l[] and vectors as columns in U[i*3+k].
 // Eigenvalues only: those of finish32 (the same expressions, compare order
 // and tie rule), ascending, in the scaled frame.
-__device__ __forceinline__ void finish32_values(const Lane32& L, float mu, float nu, float l_out[3]) {
+template <bool kSync>
+__device__ __forceinline__ void finish32_values(const Lane32& L, float mu, float nu, float l_out[3],
+                                                const unsigned sync_mask) {
   const float a1 = L.a1, a2 = L.a2, b1 = L.b1, b2 = L.b2, g = L.g;
   float l0, l1, l2;
   if (L.cls == kDiag) {
@@ -317,6 +488,7 @@ __device__ __forceinline__ void finish32_values(const Lane32& L, float mu, float
     l1 = (nu - mu) + g;
     l2 = a2 - nu;
   }
+  if constexpr (kSync) __syncwarp(sync_mask);  // the classes' lanes rejoin
   float t;
   if (l1 < l0) { t = l0; l0 = l1; l1 = t; }
   if (l2 < l1) { t = l1; l1 = l2; l2 = t; }
@@ -324,7 +496,9 @@ __device__ __forceinline__ void finish32_values(const Lane32& L, float mu, float
   l_out[0] = l0; l_out[1] = l1; l_out[2] = l2;
 }
 
-__device__ __forceinline__ void finish32(const Lane32& L, float mu, float nu, float l_out[3], float U[9], int rk[3]) {
+template <bool kSync>
+__device__ __forceinline__ void finish32(const Lane32& L, float mu, float nu, float l_out[3], float U[9], int rk[3],
+                                         const unsigned sync_mask) {
   const float a1 = L.a1, a2 = L.a2, b1 = L.b1, b2 = L.b2, g = L.g;
   float l[3], v[3][3];
   if (L.cls == kDiag) {
@@ -368,6 +542,7 @@ __device__ __forceinline__ void finish32(const Lane32& L, float mu, float nu, fl
       v[k][0] *= inv; v[k][1] *= inv; v[k][2] *= inv;
     }
   }
+  if constexpr (kSync) __syncwarp(sync_mask);  // the three classes' lanes rejoin for the common tail
   float x[3][3];
 #pragma unroll
   for (int k = 0; k < 3; k += 2) {
@@ -596,6 +771,10 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
       a_in[0] = p0.x; a_in[1] = p0.y; a_in[2] = p1.x; a_in[3] = p1.y; a_in[4] = p2.x; a_in[5] = p2.y;
       L = make_lane32<kComp>(a_in);
     }
+    // Plain form: the warp's lanes that form eigenpairs (taken where all 32
+    // are together), which rejoin after the class-specific part of the solve.
+    unsigned fin_mask = 0u;
+    if constexpr (kMode != kInline) fin_mask = __ballot_sync(0xffffffffu, L.cls != kIdle && L.cls != kNonFin);
 
     // Roots (Sec. 1.2): problem 0 is mu, problem 1 is nu (spikes swapped).
     float root[2] = {0.f, 0.f};
@@ -604,13 +783,21 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
     float ab = 0.f, pb1[2] = {0.f, 0.f}, pb2[2] = {0.f, 0.f}, pg[2] = {0.f, 0.f};
     if (L.cls == kRed) {
       ab = L.a1 - L.a2;
-      const float bb1 = L.b1 * L.b1, bb2 = L.b2 * L.b2;
-      pb1[0] = bb1; pb1[1] = bb2; pb2[0] = bb2; pb2[1] = bb1;
-      pg[0] = L.g - L.a1; pg[1] = L.a2 - L.g;
-      const float rab = rcp32(ab);
-      const float pc[2] = {pb2[0] * rab, pb2[1] * rab};
-      const float pK[2] = {-pg[0] - pc[0], -pg[1] - pc[1]};
-      roots32(ab, pb1, pb2, pg, pc, pK, root, more);
+      if constexpr (kMode != kInline) {
+        roots_setup32(L, ab, pb1, pb2, pg);
+        const P2 rab = pp(rcp32(ab)), b1p = make_float2(pb1[0], pb1[1]), b2p = make_float2(pb2[0], pb2[1]);
+        const P2 g2 = make_float2(pg[0], pg[1]);
+        const P2 pc = pmul(b2p, rab);
+        roots32x2(pp(ab), rab, b1p, b2p, g2, pc, psub(make_float2(-g2.x, -g2.y), pc), root, more);
+      } else {
+        const float bb1 = L.b1 * L.b1, bb2 = L.b2 * L.b2;
+        pb1[0] = bb1; pb1[1] = bb2; pb2[0] = bb2; pb2[1] = bb1;
+        pg[0] = L.g - L.a1; pg[1] = L.a2 - L.g;
+        const float rab = rcp32(ab);
+        const float pc[2] = {pb2[0] * rab, pb2[1] * rab};
+        const float pK[2] = {-pg[0] - pc[0], -pg[1] - pc[1]};
+        roots32(ab, pb1, pb2, pg, pc, pK, root, more);
+      }
     }
     // Rare: roots still moving after the straight-line steps, finished in
     // their own lanes (the warp runs this only when one of its roots needs it).
@@ -625,25 +812,48 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
     }
     if (L.cls == kRed) {
       if (kComp) {
-        // Exact FP32 data as double-float, then one Newton correction with
-        // a double-float f at each root.
-        const F2 abf = two_sum(L.a1, -L.a2);
-        const float rabh = rcp32(abf.h);
-        const F2 fb1 = two_prod(L.b1, L.b1), fb2 = two_prod(L.b2, L.b2);
-        const F2 fg0 = two_sum(L.g, -L.a1), fg1 = two_sum(L.a2, -L.g);
-        // c = b2 / abar and K = -(g + c) as unnormalised pairs.
-        auto div_pair = [rabh, abf](const F2 num) {
-          const float q = num.h * rabh;
-          return F2{q, ((fmaf(-q, abf.h, num.h) + num.l) - q * abf.l) * rabh};
-        };
-        auto neg_sum_pair = [](const F2 a, const F2 b) {
-          const F2 t = two_sum(a.h, b.h);
-          return F2{-t.h, -((t.l + a.l) + b.l)};
-        };
-        const F2 fc0 = div_pair(fb2), fc1 = div_pair(fb1);
-        const F2 fK0 = neg_sum_pair(fg0, fc0), fK1 = neg_sum_pair(fg1, fc1);
-        root[0] = newton_ff(abf, fb1, fb2, fg0, fc0, fK0, root[0]);
-        root[1] = newton_ff(abf, fb2, fb1, fg1, fc1, fK1, root[1]);
+        if constexpr (kMode == kInline) {
+          // Exact FP32 data as double-float, then one Newton correction with
+          // a double-float f at each root (both problems paired; the
+          // workspace form keeps the scalar code: its 47 registers leave room
+          // for the refinement CTAs beside it).
+          const F2 abf = two_sum(L.a1, -L.a2);
+          const P2 abh = pp(abf.h), abl = pp(abf.l), rabh = pp(rcp32(abf.h));
+          // spikes (b1^2, b2^2) exactly; problem 1 has them swapped
+          const P2 B = make_float2(L.b1, L.b2);
+          const P2 bh = pmul(B, B), bl = pfma(B, B, pneg(bh));
+          const P2 sbh = make_float2(bh.y, bh.x), sbl = make_float2(bl.y, bl.x);
+          P2 gh, gl;  // (g - a1, a2 - g) exactly
+          ptwo_sum(make_float2(L.g, L.a2), make_float2(-L.a1, -L.g), gh, gl);
+          // c = b2 / abar and K = -(g + c) as unnormalised pairs.
+          const P2 ch = pmul(sbh, rabh);
+          const P2 cl = pmul(pfma(pneg(ch), abl, padd(pfma(pneg(ch), abh, sbh), sbl)), rabh);
+          P2 th, tl;
+          ptwo_sum(gh, ch, th, tl);
+          const P2 Kh = pneg(th), Kl = pneg(padd(padd(tl, gl), cl));
+          const P2 xr = newton_ff2(abh, abl, bh, bl, sbh, sbl, pneg(gh), pneg(gl), ch, cl, Kh, Kl,
+                                   make_float2(root[0], root[1]));
+          root[0] = xr.x;
+          root[1] = xr.y;
+        } else {
+          const F2 abf = two_sum(L.a1, -L.a2);
+          const float rabh = rcp32(abf.h);
+          const F2 fb1 = two_prod(L.b1, L.b1), fb2 = two_prod(L.b2, L.b2);
+          const F2 fg0 = two_sum(L.g, -L.a1), fg1 = two_sum(L.a2, -L.g);
+          // c = b2 / abar and K = -(g + c) as unnormalised pairs.
+          auto div_pair = [rabh, abf](const F2 num) {
+            const float q = num.h * rabh;
+            return F2{q, ((fmaf(-q, abf.h, num.h) + num.l) - q * abf.l) * rabh};
+          };
+          auto neg_sum_pair = [](const F2 a, const F2 b) {
+            const F2 t = two_sum(a.h, b.h);
+            return F2{-t.h, -((t.l + a.l) + b.l)};
+          };
+          const F2 fc0 = div_pair(fb2), fc1 = div_pair(fb1);
+          const F2 fK0 = neg_sum_pair(fg0, fc0), fK1 = neg_sum_pair(fg1, fc1);
+          root[0] = newton_ff(abf, fb1, fb2, fg0, fc0, fK0, root[0]);
+          root[1] = newton_ff(abf, fb2, fb1, fg1, fc1, fK1, root[1]);
+        }
       }
     }
 
@@ -659,10 +869,10 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
 #pragma unroll
         for (int k = 0; k < 9; ++k) U[k] = qnan;
       } else if (!kVectors) {
-        finish32_values(L, root[0], root[1], l);
+        finish32_values<kMode == kPlain>(L, root[0], root[1], l, fin_mask);
         unscale3(l, L.e);
       } else {
-        finish32(L, root[0], root[1], l, U, rk);
+        finish32<kMode != kInline>(L, root[0], root[1], l, U, rk, fin_mask);
         if (kComp && L.cls != kDiag) {
           // the eigenvalues' gaps in ascending order (min, median, max)
           const float lo = fminf(fminf(l[0], l[1]), l[2]), hi = fmaxf(fmaxf(l[0], l[1]), l[2]);
