@@ -259,9 +259,16 @@ int syev3_selftest_wait_limit(syev3_stream_t stream);
  *        SYEV3_ARITH_RCP32, SYEV3_ARITH_SQRT32, SYEV3_ARITH_RSQRT32 -- the
  *                              FP32 hardware approximations 1/x, sqrt(x),
  *                              1/sqrt(x) (flush-to-zero) used by the FP32
- *                              zero finder.
- *   x  : device, n elements (double for RCP64, float otherwise), read.
- *   y  : device, n elements of the same type, written; may not overlap x.
+ *                              zero finder;
+ *        SYEV3_ARITH_F2D, SYEV3_ARITH_D2F -- float to double (exact) and
+ *                              double to float (round to nearest even),
+ *                              computed on the integer pipes by the FP64
+ *                              kernels and the FP64 refinement; the IEEE
+ *                              results bit for bit.
+ *   x  : device, n elements (double for RCP64 and D2F, float otherwise),
+ *        read.
+ *   y  : device, n elements (double for RCP64 and F2D, float otherwise),
+ *        written; may not overlap x.
  *   n  : >= 0.
  * Returns SYEV3_EINVAL (bad op, n < 0, NULL or misaligned buffers) or
  * SYEV3_ECUDA; asynchronous on `stream`. */
@@ -269,6 +276,8 @@ int syev3_selftest_wait_limit(syev3_stream_t stream);
 #define SYEV3_ARITH_RCP32 1
 #define SYEV3_ARITH_SQRT32 2
 #define SYEV3_ARITH_RSQRT32 3
+#define SYEV3_ARITH_F2D 4
+#define SYEV3_ARITH_D2F 5
 
 int syev3_selftest_arith(int op, const void* x, void* y, int64_t n, syev3_stream_t stream);
 

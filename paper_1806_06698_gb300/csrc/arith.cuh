@@ -90,6 +90,42 @@ __device__ __forceinline__ double flip_sign(double x, int flip) {
 // 2^k as a float for -126 <= k <= 127.
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
 
+// FP32 <-> FP64 conversions on the integer pipes.  On this GPU a conversion
+// instruction between the two formats issues to the FP64 pipe, the scarce
+// one (2 lanes per clock per SM), while the integer pipes have room to
+// spare in the FP64-bound kernels.  Zero and normal numbers -- everything
+// the kernels convert in practice -- are converted on 32-bit words; the
+// rest (subnormal results or operands, infinities, NaN) take the hardware
+// conversion in a branch.  The results are the IEEE ones bit for bit
+// (checked against the hardware conversions by syev3_selftest_arith).
+//
+// float -> double, exact: a normal float's exponent is rebiased by
+// 1023 - 127 = 896 and its 23-bit fraction split over the two words.
+__device__ __forceinline__ double f2d_exact(const float x) {
+  const unsigned u = __float_as_uint(x), a = u & 0x7fffffffu;
+  if (a - 0x00800000u < 0x7f000000u)  // normal
+    return __hiloint2double((int)((u & 0x80000000u) | ((a >> 3) + (896u << 20))), (int)(a << 29));
+  if (a == 0u) return __hiloint2double((int)u, 0);
+  return (double)x;
+}
+
+// double -> float, rounded to nearest, ties to even (the IEEE default): in
+// the float normal range the top 23 fraction bits are kept and the 29 below
+// decide the rounding; a carry out of the fraction steps the exponent (up to
+// infinity, the correctly rounded overflow).
+__device__ __forceinline__ float d2f_rn(const double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned E = (hi >> 20) & 0x7ffu;
+  if (E - 897u <= 253u) {  // float exponent 1..254
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29), rem = lo & 0x1fffffffu;
+    unsigned f = ((E - 896u) << 23) + m;
+    f += (unsigned)(rem > 0x10000000u) | ((unsigned)(rem == 0x10000000u) & (f & 1u));
+    return __uint_as_float((hi & 0x80000000u) | f);
+  }
+  if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(hi);  // +-0
+  return __double2float_rn(x);
+}
+
 // ---------------------------------------------------------------------------
 // Double-float arithmetic: an unevaluated sum h + l of two floats, built on
 // the error-free transformations TwoSum (Knuth, TAOCP vol. 2, 4.2.2),

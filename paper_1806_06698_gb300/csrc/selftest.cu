@@ -1,8 +1,9 @@
 // selftest.cu -- measurement and self-test kernels of libsyev3 (sm_103a).
 //
 // Neither is part of the method of the paper.  k_arith_probe evaluates the
-// kernels' own approximate arithmetic (arith.cuh) elementwise, so that tests
-// can check the error bounds the solver relies on against IEEE results;
+// kernels' own arithmetic helpers (arith.cuh) elementwise, so that tests can
+// check them against IEEE results (the approximations' error bounds, the
+// integer-pipe conversions' exactness);
 // k_dfma_probe runs long chains of independent FP64 fused multiply-adds, the
 // operation rate that bounds the FP64 solver, so the benchmark can report
 // its roofline against a measured FP64 peak.
@@ -22,6 +23,10 @@ __global__ void k_arith_probe(int op, const void* __restrict__ x, void* __restri
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     if (op == SYEV3_ARITH_RCP64) {
       static_cast<double*>(y)[i] = rcp64(static_cast<const double*>(x)[i]);
+    } else if (op == SYEV3_ARITH_F2D) {
+      static_cast<double*>(y)[i] = f2d_exact(static_cast<const float*>(x)[i]);
+    } else if (op == SYEV3_ARITH_D2F) {
+      static_cast<float*>(y)[i] = d2f_rn(static_cast<const double*>(x)[i]);
     } else {
       const float v = static_cast<const float*>(x)[i];
       float r;

@@ -198,14 +198,15 @@ __device__ __forceinline__ int finish64(const double ab, const double b1, const 
   // iteration.
   const double b = fma(f, r1, fp);
   if (hi_mag(b) >= hi_pow2(126)) return 1;  // b >= 2^126 (b >= 1 always)
-  const float rbf = rcp32((float)b);
-  const double q0 = f * (double)rbf;
-  const double fr = fma(fma(-b, q0, f), (double)rbf, q0);  // f/b
-  const float xf = (float)x, r1f = rcp32(xf), r2f = rcp32(xf + abf);
+  const float rbf = rcp32(d2f_rn(b));
+  const double rbd = f2d_exact(rbf);
+  const double q0 = f * rbd;
+  const double fr = fma(fma(-b, q0, f), rbd, q0);  // f/b
+  const float xf = d2f_rn(x), r1f = rcp32(xf), r2f = rcp32(xf + abf);
   const float w0f = fmaf(b2f * r2f * abf, r2f * r2f, 1.f);  // omega_0
-  const float zf = (-4.f * w0f) * (r1f * rbf) * (float)fr;
+  const float zf = (-4.f * w0f) * (r1f * rbf) * d2f_rn(fr);
   if (!(fabsf(zf) < 0x1p-12f)) return 1;
-  const double delta = fma(fr, (double)(zf * fmaf(zf, 0.125f, -0.25f)), fr);
+  const double delta = fma(fr, f2d_exact(zf * fmaf(zf, 0.125f, -0.25f)), fr);
   // delta >= x/2: the zero of phi_j is far below x; leave it to the full iteration.
   if (dbits(delta) >= dbits(x) - (1ull << 52)) return 1;
   const double xn = x - delta;
@@ -239,9 +240,9 @@ __device__ __forceinline__ int finish64(const double ab, const double b1, const 
   // f' only scales the threshold: FP32 is enough, capped at 2^120 (an f'
   // under the true one, or an FP32 x that underflowed, only makes the test
   // stricter and leaves the root to the full iteration).
-  const float xf2 = (float)x, q1 = rcp32(xf2), q2 = rcp32(xf2 + abf);
+  const float xf2 = d2f_rn(x), q1 = rcp32(xf2), q2 = rcp32(xf2 + abf);
   const float fpf = fminf(fmaf(b2f * q2, q2, fmaf(b1f * q1, q1, 1.f)), 0x1p120f);
-  if (dbits(f) < dbits(x * (double)fpf) - (51ull << 52)) return 0;
+  if (dbits(f) < dbits(x * f2d_exact(fpf)) - (51ull << 52)) return 0;
   return 1;
 }
 

@@ -188,10 +188,11 @@ int syev3_selftest_wait_limit(syev3_stream_t stream) {
 }
 
 int syev3_selftest_arith(int op, const void* x, void* y, int64_t n, syev3_stream_t stream) {
-  if (op < SYEV3_ARITH_RCP64 || op > SYEV3_ARITH_RSQRT32 || n < 0) return SYEV3_EINVAL;
+  if (op < SYEV3_ARITH_RCP64 || op > SYEV3_ARITH_D2F || n < 0) return SYEV3_EINVAL;
   if (n == 0) return SYEV3_OK;
-  const size_t es = op == SYEV3_ARITH_RCP64 ? 8 : 4;
-  if (x == nullptr || y == nullptr || !aligned(x, es) || !aligned(y, es) || overlap(x, n * es, y, n * es) ||
+  const size_t xs = (op == SYEV3_ARITH_RCP64 || op == SYEV3_ARITH_D2F) ? 8 : 4;
+  const size_t ys = (op == SYEV3_ARITH_RCP64 || op == SYEV3_ARITH_F2D) ? 8 : 4;
+  if (x == nullptr || y == nullptr || !aligned(x, xs) || !aligned(y, ys) || overlap(x, n * xs, y, n * ys) ||
       !device_accessible(x) || !device_accessible(y))
     return SYEV3_EINVAL;
   const cudaError_t e = syev3::launch_arith_probe(op, x, y, n, reinterpret_cast<cudaStream_t>(stream));

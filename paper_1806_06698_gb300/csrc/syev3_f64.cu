@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
                            hi_mag(ab) >= hi_pow2(-100);  // (all three >= 0)
       float sd[2] = {0.f, 0.f};
       double pc[2] = {0.0, 0.0}, pK[2] = {0.0, 0.0};
-      const float fab = (float)ab, fb1[2] = {(float)pb1[0], (float)pb1[1]}, fb2[2] = {(float)pb2[0], (float)pb2[1]};
+      const float fab = d2f_rn(ab), fb1[2] = {d2f_rn(pb1[0]), d2f_rn(pb1[1])}, fb2[2] = {d2f_rn(pb2[0]), d2f_rn(pb2[1])};
       if (fp32_ok) {
         const double rab = rcp64(ab);
 #pragma unroll
@@ -304,13 +304,13 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f64(const double* __restrict__ A
           pc[k] = pb2[k] * rab;
           pK[k] = -pg[k] - pc[k];
         }
-        const float fg[2] = {(float)pg[0], (float)pg[1]};
-        const float fc[2] = {(float)pc[0], (float)pc[1]}, fK[2] = {(float)pK[0], (float)pK[1]};
+        const float fg[2] = {d2f_rn(pg[0]), d2f_rn(pg[1])};
+        const float fc[2] = {d2f_rn(pc[0]), d2f_rn(pc[1])}, fK[2] = {d2f_rn(pK[0]), d2f_rn(pK[1])};
         seed32x2(fab, fb1, fb2, fg, fc, fK, sd);
       }
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        double x = (double)sd[k];
+        double x = f2d_exact(sd[k]);
         int st = 2;
         // 2^-900 <= x <= 2^100 (x >= 0): the range finish64 assumes.
         if (hi_mag(x) >= hi_pow2(-900) && dbits(x) <= dbits(0x1p+100))

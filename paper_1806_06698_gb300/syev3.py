@@ -225,16 +225,19 @@ def device_flags() -> int:
 
 
 # Operations of syev3_selftest_arith (include/syev3.h).
-ARITH_RCP64, ARITH_RCP32, ARITH_SQRT32, ARITH_RSQRT32 = 0, 1, 2, 3
+ARITH_RCP64, ARITH_RCP32, ARITH_SQRT32, ARITH_RSQRT32, ARITH_F2D, ARITH_D2F = 0, 1, 2, 3, 4, 5
 
 
 def selftest_arith(op: int, x: torch.Tensor, stream=None) -> torch.Tensor:
-    """The kernels' approximate reciprocal / square root helpers applied to
-    the device tensor x (float64 for ARITH_RCP64, float32 otherwise)."""
-    want = torch.float64 if op == ARITH_RCP64 else torch.float32
+    """The kernels' arithmetic helpers applied to the device tensor x:
+    reciprocal / square root approximations (float64 in and out for
+    ARITH_RCP64, float32 otherwise) and the integer-pipe conversions
+    (ARITH_F2D: float32 -> float64, ARITH_D2F: float64 -> float32)."""
+    want = torch.float64 if op in (ARITH_RCP64, ARITH_D2F) else torch.float32
+    out = torch.float64 if op in (ARITH_RCP64, ARITH_F2D) else torch.float32
     if not x.is_cuda or x.dtype != want or not x.is_contiguous():
         raise ValueError(f"x must be a contiguous {want} CUDA tensor")
-    y = torch.empty_like(x)
+    y = torch.empty(x.shape, dtype=out, device=x.device)
     _check(_load().syev3_selftest_arith(int(op), _ptr(x), _ptr(y), x.numel(), _stream(stream)),
            "syev3_selftest_arith")
     return y
