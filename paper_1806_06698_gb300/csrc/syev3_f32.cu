@@ -26,6 +26,14 @@
 // appends them to a list in a workspace for k_refine_f32, which runs beside
 // the FP32 solve on a second stream for large batches).
 //
+// The two root problems of a lane (mu and nu) run the same expressions, so
+// their arithmetic is paired on the packed FP32 instructions (two correctly
+// rounded operations per instruction); reciprocals, roots, comparisons and
+// selections stay per half.  Lanes of the three classes (diagonal, deflated,
+// reduced) in one warp take different branches of the solve; an explicit
+// __syncwarp over the lanes that form eigenpairs rejoins them for the common
+// tail (without it the warp was measured to stay split there).
+//
 // Memory path as in the FP64 kernel: tiles of kTPB records (24 B each) by
 // 1-D bulk copy into shared memory, double-buffered on mbarriers; results
 // staged in shared memory and written with 16-byte stores.  The plain form
@@ -61,9 +69,9 @@ constexpr float kTinySpike32 = 0x1p-60f;  // spikes below this are zeroed (beta-
 constexpr float kNearDefl = 2.0f;         // near-deflated: test sides within this factor
 constexpr float kClusterTau = 0x1p-23f;   // clustered: relative gap below this
 constexpr double kResidualTol = 16.0 * 0x1p-23;  // FP64 residual check, times ||A||_F
-// Plain form: a last zero-finder move above kMoveTol x (relative error of
-// order kMoveTol^3 = 2^-24 after the cubically convergent step) sends the
-// root to further steps.
+// Plain and workspace forms: a last zero-finder move above kMoveTol x
+// (relative error of order kMoveTol^3 = 2^-24 after the cubically
+// convergent step) sends the root to further steps.
 constexpr float kMoveTol = 0x1p-8f;
 constexpr int kPlain = 0, kInline = 1, kDeferred = 2;  // modes of k_syev3_f32
 
@@ -304,9 +312,9 @@ __device__ __forceinline__ P2 bg_step32x2(const P2 ab, const P2 b1, const P2 b2,
 }
 
 // The schedule of roots32x2 (below) one problem at a time, for the
-// compensated forms: their builds keep 40 registers, room for the FP64
-// refinement CTAs that run beside them.  more[k] as in roots32x2, for a move
-// above 2^-12 x; these forms finish such roots in the warp, right after.
+// compensated form with its refinement inside the kernel.  more[k] as in
+// roots32x2, for a move above 2^-12 x; the warp finishes such roots right
+// after.
 __device__ __forceinline__ void roots32(const float ab, const float b1[2], const float b2[2], const float g[2],
                                         const float c[2], const float K[2], float x[2], bool more[2]) {
 #pragma unroll
@@ -771,8 +779,9 @@ __global__ void __launch_bounds__(kTPB) k_syev3_f32(const float* __restrict__ A,
       a_in[0] = p0.x; a_in[1] = p0.y; a_in[2] = p1.x; a_in[3] = p1.y; a_in[4] = p2.x; a_in[5] = p2.y;
       L = make_lane32<kComp>(a_in);
     }
-    // Plain form: the warp's lanes that form eigenpairs (taken where all 32
-    // are together), which rejoin after the class-specific part of the solve.
+    // Plain and workspace forms: the warp's lanes that form eigenpairs (taken
+    // where all 32 are together), which rejoin after the class-specific part
+    // of the solve.
     unsigned fin_mask = 0u;
     if constexpr (kMode != kInline) fin_mask = __ballot_sync(0xffffffffu, L.cls != kIdle && L.cls != kNonFin);
 
