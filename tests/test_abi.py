@@ -109,3 +109,24 @@ def test_workspace_entry_point_argument_checks(lib):
     assert call(A, 1000, lam, None, syev3.SYEV3_F32_COMPENSATED, None, A, need, None) == syev3.SYEV3_EINVAL
     # n == 0 is a no-op
     assert call(None, 0, None, None, syev3.SYEV3_F32_COMPENSATED, None, None, 0, None) == syev3.SYEV3_OK
+
+
+def test_selftest_arith_argument_checks(lib):
+    from paper_1806_06698_gb300 import syev3
+
+    vp = ctypes.c_void_p
+    call = lib.syev3_selftest_arith
+    # every operation the header names (the reciprocal and root helpers and
+    # the two integer-pipe conversions) takes n == 0 as a no-op
+    for op in (syev3.ARITH_RCP64, syev3.ARITH_RCP32, syev3.ARITH_SQRT32, syev3.ARITH_RSQRT32, syev3.ARITH_F2D,
+               syev3.ARITH_D2F):
+        assert call(op, None, None, 0, None) == syev3.SYEV3_OK, op
+    # an unknown operation or n < 0: EINVAL before any CUDA call
+    assert call(syev3.ARITH_D2F + 1, vp(4096), vp(8192), 4, None) == syev3.SYEV3_EINVAL
+    assert call(-1, vp(4096), vp(8192), 4, None) == syev3.SYEV3_EINVAL
+    assert call(syev3.ARITH_F2D, vp(4096), vp(8192), -1, None) == syev3.SYEV3_EINVAL
+    # the conversions read and write different element sizes: a double side
+    # misaligned for 8 bytes, or output overlapping input, is rejected
+    assert call(syev3.ARITH_F2D, vp(4096), vp(8196), 4, None) == syev3.SYEV3_EINVAL
+    assert call(syev3.ARITH_D2F, vp(4100), vp(8192), 4, None) == syev3.SYEV3_EINVAL
+    assert call(syev3.ARITH_F2D, vp(4096), vp(4104), 4, None) == syev3.SYEV3_EINVAL
